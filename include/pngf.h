@@ -1,0 +1,189 @@
+/*
+ * pngf.h - C ABI of the PNGF direct-binary-search (DBS) hot path on one GPU.
+ *
+ * Method (arXiv 2501.18054, "Near real-time full-wave inverse design of
+ * electromagnetic devices"): a precomputed numerical Green function G (Eq. 3)
+ * reduces the evaluation of a candidate design to a linear system over the
+ * design region only (Eqs. 2 and 7; generalised materials and the field form
+ * in Supplementary Note 4).  DBS flips one pixel at a time and keeps the flip
+ * if the objective improves (section "Direct binary search optimization",
+ * Supplementary Fig. 1).  A flip is a rank-1 change of the system matrix, so
+ * every candidate is scored exactly through the Woodbury / Sherman-Morrison
+ * identity (Eq. 9, scored through R and S as in Eqs. 11-14) and the maintained
+ * inverse is corrected rank-1 when a flip is kept (Eq. 9; cost in
+ * Supplementary Note 3).
+ *
+ * Field-form notation used throughout (one unknown per pixel, 2D TM):
+ *   G    = G_dd   (n_d x n_d)  design-to-design Green function, complex symmetric
+ *   G_od          (n_o x n_d)  design-to-port functionals (the paper's G_obj)
+ *   c_d, c_o                   incident field on the pixels / at the ports
+ *                              (the paper's e_inc and x_inc)
+ *   v_k  = dv_k * b_k          contrast of pixel k, b in {0,1}^n_d (the
+ *                              paper's Y, Supplementary Note 4)
+ *   M    = I - G diag(v)       reduced system, M e = c_d
+ *   o    = c_o + G_od (v .* e) port amplitudes (the paper's x_obj, Eq. 5)
+ *   S_p  = (o_p - s_off_p) * s_scale_p,  f = objective(S)
+ *   W    = M^-1 G              maintained inverse (the paper's C~^-1 of the
+ *                              field form, Supplementary Note 4)
+ *   T    = G_od (I + V W)      port projection of W (the paper's R, Eq. 11)
+ * Flipping pixel k changes v_k by delta; with d_k = 1 - delta W_kk and
+ * alpha = delta / d_k the candidate ports are o + alpha e_k T[:,k] (Eq. 14)
+ * and an accepted flip applies W += alpha c c^T, c = W[:,k] (Eq. 9).
+ *
+ * Conventions of every call:
+ *  - Complex numbers are interleaved (re, im) doubles: "c128".
+ *  - Every array pointer is a DEVICE pointer unless its comment says "host".
+ *    The caller owns every array.  The library keeps the pointers to G_dd,
+ *    G_od, c_d, c_o and dv given to pngf_create; they must stay valid and
+ *    unchanged until pngf_destroy.  It allocates no device memory: all scratch
+ *    lives in the caller's workspace (size from pngf_workspace_size).
+ *  - Work is ordered on the stream given to pngf_create.  Calls returning
+ *    device results do not synchronize; calls with host outputs do.
+ *  - Every call returns a pngf_status and never aborts the process.  A
+ *    failure detected on the device (singular pivot, non-finite value, a wait
+ *    that timed out) is latched in the workspace and returned by the next call
+ *    that synchronizes (pngf_eval_ports, pngf_sync).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef PNGF_H
+#define PNGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pngf_stream; /* a cudaStream_t; NULL = default stream */
+typedef struct pngf_ctx pngf_ctx;        /* opaque, host-side handle */
+
+typedef enum {
+  PNGF_OK = 0,
+  PNGF_EINVAL = 1,        /* bad argument (size, pointer, alignment, mode) */
+  PNGF_ENOMEM = 2,        /* workspace smaller than pngf_workspace_size */
+  PNGF_ECUDA = 3,         /* a CUDA runtime call failed */
+  PNGF_ESINGULAR = 4,     /* zero pivot in the factorisation of M */
+  PNGF_ENOTFACTORED = 5,  /* pngf_factor has not run on this context */
+  PNGF_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+  PNGF_ENUMERIC = 7,      /* non-finite value met on the device */
+  PNGF_ECAPACITY = 8      /* trace buffer full (the sweep stopped early) */
+} pngf_status;
+
+typedef enum { PNGF_FP64 = 0, PNGF_MIXED = 1 } pngf_precision;
+typedef enum { PNGF_FIRST_IMPROVEMENT = 0, PNGF_BEST_IMPROVEMENT = 1 } pngf_dbs_mode;
+typedef enum {
+  PNGF_OBJ_MAX_WEIGHTED_POWER = 0, /* maximise sum_p w_p |S_p|^2 */
+  PNGF_OBJ_MIN_INSERTION_LOSS = 1  /* minimise sum_p w_p (1 - |S_p|)^2 (Supplementary Note 9) */
+} pngf_objective;
+
+#define PNGF_MAX_PORTS 8
+
+typedef struct {
+  int32_t n_d;        /* design pixels, 1 <= n_d <= 32768 */
+  int32_t n_o;        /* ports, 1 <= n_o <= PNGF_MAX_PORTS */
+  int32_t precision;  /* pngf_precision */
+  int32_t mode;       /* pngf_dbs_mode */
+  int32_t objective;  /* pngf_objective */
+  int32_t refresh_k;  /* FP64 iterative-refinement refresh of e, T, o every refresh_k
+                         accepted flips (0 = never) */
+  int32_t delay_r;    /* PNGF_MIXED: flips accumulated before the maintained inverse is
+                         updated in one rank-delay_r product (1..128); ignored for FP64 */
+  int32_t n_ctas;     /* persistent sweep grid (0 = one per SM, capped by occupancy) */
+  double tau;         /* accept iff gain > tau * max(|f|, 1e-30) */
+  double obj_weights[PNGF_MAX_PORTS]; /* w_p */
+  double s_off[2 * PNGF_MAX_PORTS];   /* c128 per port */
+  double s_scale[2 * PNGF_MAX_PORTS]; /* c128 per port */
+} pngf_config;
+
+/* Bytes of device workspace a context with this configuration needs. */
+pngf_status pngf_workspace_size(const pngf_config* cfg, size_t* bytes);
+
+/*
+ * Bind the precomputed inputs (Eqs. 3 and 5; section "Precomputation"):
+ *   G_dd  c128 n_d x n_d row-major, complex symmetric (reciprocal background)
+ *   G_od  c128 n_o x n_d row-major
+ *   c_d   c128 n_d;  c_o  c128 n_o
+ *   dv    c128 n_d: contrast of a pixel that is "on" (k^2 (eps_on - eps_off))
+ * workspace: >= pngf_workspace_size bytes, 256-byte aligned, device memory.
+ * Nothing is computed until pngf_factor.  *out receives a host handle.
+ */
+pngf_status pngf_create(const pngf_config* cfg, const double* G_dd, const double* G_od,
+                        const double* c_d, const double* c_o, const double* dv,
+                        void* workspace, size_t workspace_bytes, pngf_stream stream,
+                        pngf_ctx** out);
+
+/*
+ * Factor M = I - G diag(dv .* b) once (blocked LU with partial pivoting, FP64)
+ * and form the maintained state W = M^-1 G, e = M^-1 c_d, T = G_od (I + V W),
+ * o = c_o + G_od (v .* e) (the paper's initial inversion of C_0,
+ * section "Direct binary search optimization").  b: uint8 n_d (0/1).
+ * Returns PNGF_ESINGULAR (via the latched status) if a pivot is exactly 0.
+ */
+pngf_status pngf_factor(pngf_ctx* ctx, const uint8_t* b);
+
+/*
+ * Score candidate flips against the current state without changing it
+ * (Eq. 14): for each listed pixel k, f_new[i] = objective after flipping k.
+ *   pixels  int32 n (device), 0 <= pixels[i] < n_d
+ *   f_new   double n (device, out)
+ *   o_new   c128 n x n_o (device, out) or NULL
+ * A candidate with |d_k| < 1e-14 gets f_new = NaN.
+ */
+pngf_status pngf_score_flips(pngf_ctx* ctx, const int32_t* pixels, int32_t n, double* f_new,
+                             double* o_new);
+
+/* Keep the flip of one pixel: rank-1 update of W, T, e, o, v, b (Eq. 9). */
+pngf_status pngf_accept_flip(pngf_ctx* ctx, int32_t pixel);
+
+/*
+ * Run direct binary search on the device: up to n_sweeps passes over the
+ * pixels; a pass that keeps no flip ends the search (converged).
+ *   order     int32 n_sweeps x n_d (device): visiting order of each pass, each
+ *             row a permutation of 0..n_d-1; NULL = raster order 0..n_d-1.
+ *             FIRST mode keeps the first improving flip in visiting order
+ *             (sequential DBS semantics); BEST mode keeps the best improving
+ *             flip of the whole region per step (ties -> lowest pixel index),
+ *             ignores order, and n_sweeps bounds its number of steps (each
+ *             step evaluates all n_d pixels).
+ *   trace     int32 trace_cap x 4 (device, out): per kept flip
+ *             (sweep, position, pixel, 0); may be NULL if trace_cap == 0
+ *   trace_f   double trace_cap (device, out): objective after each kept flip, or NULL
+ *   counters  int64 8 (device, out): [0] kept flips, [1] attempted flips
+ *             (evaluations in sequential semantics), [2] sweeps run,
+ *             [3] converged (0/1), [4] refreshes, [5] flushes, [6] status, [7] 0
+ * Kept flips past trace_cap are still applied but not recorded; [6] is then
+ * PNGF_ECAPACITY.  The state stays on the device for further calls.
+ */
+pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order,
+                           int32_t* trace, double* trace_f, int32_t trace_cap,
+                           int64_t* counters);
+
+/* Current port amplitudes (c128 n_o, host) and objective (host); synchronizes. */
+pngf_status pngf_eval_ports(pngf_ctx* ctx, double* o_host, double* f_host);
+
+/* Copy the current design (uint8 n_d, device). */
+pngf_status pngf_get_design(pngf_ctx* ctx, uint8_t* b);
+
+/*
+ * Read back the maintained state (device outputs, any may be NULL):
+ *   W c128 n_d x n_d (FP64 precision only, else PNGF_EINVAL if non-NULL),
+ *   diag_W c128 n_d, e c128 n_d, T c128 n_o x n_d, o c128 n_o.
+ */
+pngf_status pngf_get_state(pngf_ctx* ctx, double* W, double* diag_W, double* e, double* T,
+                           double* o);
+
+/* Save the current state inside the workspace / restore it (same stream). */
+pngf_status pngf_snapshot(pngf_ctx* ctx);
+pngf_status pngf_restore(pngf_ctx* ctx);
+
+/* Synchronize the stream and return the latched device status (then clear it). */
+pngf_status pngf_sync(pngf_ctx* ctx);
+
+const char* pngf_status_string(pngf_status s);
+void pngf_destroy(pngf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNGF_H */

@@ -1,0 +1,201 @@
+"""Pins of the CPU oracle to things other than itself (CPU only).
+
+* the reduced system against a direct sparse solve of the full modified FDFD
+  structure (the paper's own accuracy check, Supplementary Note 8: the PNGF
+  result agrees with the full solver to ~10 digits in double precision);
+* the one-pixel closed form and the zero-contrast special case;
+* brute-force enumeration of every design of a tiny region: the end state of
+  the oracle's DBS is one-flip locally optimal, its trajectory only improves,
+  and BEST mode takes the enumerated best neighbour every step;
+* planted mistakes in the oracle are caught by these pins.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_2501_18054_gb300 import workloads as W
+import oracle as O
+
+
+@pytest.fixture(scope="module")
+def fdfd64():
+    return W.make_fdfd_case("fdfd64")
+
+
+@pytest.fixture(scope="module")
+def metal128():
+    return W.make_fdfd_case("fdfd128_metal")
+
+
+def _full_structure(case, b):
+    spec = W.SPECS[case.name]
+    eps = W._eps_grid(spec)
+    x0, y0, dx, dy = spec.design
+    eps[x0:x0 + dx, y0:y0 + dy] = np.where(np.asarray(b).reshape(dx, dy) == 1, spec.eps_on, spec.eps_off)
+    E, o = W.solve_full(spec, eps)
+    return E[W._design_nodes(spec)], o
+
+
+@pytest.mark.parametrize("name,seed", [("fdfd64", 3), ("fdfd64", 4), ("fdfd128_metal", 3)])
+def test_reduced_system_equals_full_fdfd(name, seed, fdfd64, metal128):
+    case = fdfd64 if name == "fdfd64" else metal128
+    b = W.random_design(case.n_d, seed)
+    ev = O.evaluate(O.Problem.from_case(case), b)
+    e_full, o_full = _full_structure(case, b)
+    assert np.max(np.abs(ev.e - e_full)) <= 1e-10 * np.max(np.abs(e_full))
+    assert np.max(np.abs(ev.o - o_full)) <= 1e-10 * np.max(np.abs(o_full))
+
+
+def test_one_pixel_closed_form(fdfd64):
+    s = fdfd64.sub_case([57])
+    p = O.Problem.from_case(s)
+    ev = O.evaluate(p, np.array([1], np.uint8))
+    g, c, v = s.G_dd[0, 0], s.c_d[0], s.dv[0]
+    e = c / (1.0 - g * v)
+    assert abs(ev.e[0] - e) <= 1e-15 * abs(e)
+    o = s.c_o + s.G_od[:, 0] * v * e
+    assert np.max(np.abs(ev.o - o)) <= 1e-15 * np.max(np.abs(o))
+
+
+def test_zero_contrast_leaves_the_incident_field(fdfd64):
+    p = O.Problem.from_case(fdfd64)
+    p.dv = np.zeros_like(p.dv)
+    ev = O.evaluate(p, W.random_design(fdfd64.n_d, 1))
+    assert np.array_equal(ev.o, fdfd64.c_o)
+    assert np.array_equal(ev.e, fdfd64.c_d)
+
+
+def test_empty_design_is_the_incident_field(fdfd64):
+    ev = O.evaluate(O.Problem.from_case(fdfd64), np.zeros(fdfd64.n_d, np.uint8))
+    assert np.array_equal(ev.o, fdfd64.c_o)
+
+
+def test_objectives():
+    S = np.array([0.6 + 0.0j, 0.0 + 0.8j])
+    assert O.objective(S, O.OBJ_MAX_WEIGHTED_POWER, np.array([0.0, 1.0])) == pytest.approx(0.64, abs=1e-15)
+    assert O.objective(S, O.OBJ_MIN_INSERTION_LOSS, np.array([0.0, 1.0])) == pytest.approx(0.04, abs=1e-15)
+    assert O.improvement(2.0, 1.0, O.OBJ_MAX_WEIGHTED_POWER) == 1.0
+    assert O.improvement(2.0, 1.0, O.OBJ_MIN_INSERTION_LOSS) == -1.0
+
+
+def _tiny(fdfd64, n_pix=12):
+    # a 3 x 4 block in the middle of the 10 x 10 region (pixels k = 10*x + y)
+    idx = [10 * x + y for x in range(3, 6) for y in range(3, 7)][:n_pix]
+    return fdfd64.sub_case(idx)
+
+
+def _enumerate(p):
+    n = p.n_d
+    fs = np.empty(2 ** n)
+    for m in range(2 ** n):
+        b = np.array([(m >> i) & 1 for i in range(n)], np.uint8)
+        fs[m] = O.evaluate(p, b).f
+    return fs
+
+
+def _code(b):
+    return int(sum(int(x) << i for i, x in enumerate(b)))
+
+
+@pytest.fixture(scope="module")
+def tiny(fdfd64):
+    s = _tiny(fdfd64)
+    p = O.Problem.from_case(s)
+    return s, p, _enumerate(p)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_dbs_end_state_is_locally_optimal(tiny, seed):
+    s, p, fs = tiny
+    b0 = W.random_design(s.n_d, seed)
+    tau = 1e-9
+    res = O.dbs(p, b0, W.raster_order(s.n_d, 50), tau=tau)
+    assert res.sweeps_done < 50  # converged
+    f_end = fs[_code(res.b)]
+    assert res.f == f_end
+    for k in range(s.n_d):
+        nb = res.b.copy(); nb[k] ^= 1
+        assert fs[_code(nb)] - f_end <= tau * abs(f_end)
+    # the trajectory only improves, and each kept flip is the first improving one in order
+    f = fs[_code(b0)]
+    b = b0.copy()
+    last = (-1, -1)
+    for (sw, t, k, f_after) in res.accepted:
+        assert (sw, t) > last
+        last = (sw, t)
+        b[k] ^= 1
+        assert f_after == fs[_code(b)] and f_after > f + tau * abs(f)
+        f = f_after
+    assert fs.max() >= f_end
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_dbs_best_mode_takes_the_best_neighbour(tiny, seed):
+    s, p, fs = tiny
+    b = W.random_design(s.n_d, seed)
+    res = O.dbs(p, b, W.raster_order(s.n_d, 100), tau=1e-9, mode=O.BEST_IMPROVEMENT)
+    for (_, _, k, f_after) in res.accepted:
+        nbr = []
+        for j in range(s.n_d):
+            nb = b.copy(); nb[j] ^= 1
+            nbr.append(fs[_code(nb)])
+        assert k == int(np.argmax(nbr))
+        b[k] ^= 1
+        assert f_after == fs[_code(b)]
+
+
+def test_dbs_shuffled_order_visits_every_pixel(tiny):
+    s, p, fs = tiny
+    order = W.shuffled_order(s.n_d, 40, seed=3)
+    res = O.dbs(p, W.random_design(s.n_d, 9), order, tau=1e-9)
+    for (sw, t, k, _) in res.accepted:
+        assert order[sw, t] == k
+    f_end = fs[_code(res.b)]
+    for k in range(s.n_d):
+        nb = res.b.copy(); nb[k] ^= 1
+        assert fs[_code(nb)] - f_end <= 1e-9 * abs(f_end)
+
+
+def test_dbs_counts_every_visited_position(fdfd64):
+    s = _tiny(fdfd64, 8)
+    p = O.Problem.from_case(s)
+    res = O.dbs(p, W.random_design(8, 2), W.raster_order(8, 20), tau=1e-9)
+    assert res.n_evals == res.sweeps_done * 8
+    res2 = O.dbs(p, W.random_design(8, 2), W.raster_order(8, 20), tau=1e-9, max_evals=5)
+    assert res2.n_evals == 5
+
+
+def test_maintained_quantities_definitions(fdfd64):
+    """W = M^-1 G and T = G_od (I + V W) against their defining systems."""
+    s = _tiny(fdfd64)
+    b = W.random_design(s.n_d, 1)
+    v = s.dv * b
+    M = O.system_matrix(s.G_dd, v)
+    Wm = O.maintained_inverse(s.G_dd, v)
+    assert np.max(np.abs(M @ Wm - s.G_dd)) < 1e-13
+    T = O.port_projection(s.G_dd, s.G_od, v)
+    # T M^T = G_od (M^-T = I + V W since W is symmetric)
+    assert np.max(np.abs(T @ M.T - s.G_od)) < 1e-13
+    assert np.max(np.abs(Wm - Wm.T)) < 1e-13
+
+
+def test_planted_mistakes_are_caught(fdfd64, monkeypatch):
+    """A plausible slip in the oracle fails the full-structure pin."""
+    case = fdfd64
+    b = W.random_design(case.n_d, 3)
+    e_full, o_full = _full_structure(case, b)
+    p = O.Problem.from_case(case)
+    plants = {
+        "sign of the contrast term": lambda G, v: np.eye(G.shape[0], dtype=complex) + G * v[None, :],
+        "transposed contrast": lambda G, v: np.eye(G.shape[0], dtype=complex) - G * v[:, None],
+        "dropped identity": lambda G, v: -G * v[None, :] + 1e-3 * np.eye(G.shape[0]),
+    }
+    for what, bad in plants.items():
+        monkeypatch.setattr(O.pngf_oracle, "system_matrix", bad)
+        ev = O.evaluate(p, b)
+        assert np.max(np.abs(ev.o - o_full)) > 1e-6 * np.max(np.abs(o_full)), what
+    monkeypatch.undo()
+    monkeypatch.setattr(O.pngf_oracle, "port_amplitudes", lambda God, co, v, e: co + God @ e)
+    ev = O.evaluate(p, b)
+    assert np.max(np.abs(ev.o - o_full)) > 1e-6 * np.max(np.abs(o_full)), "dropped V in ports"
