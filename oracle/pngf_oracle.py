@@ -180,7 +180,7 @@ class DbsResult:
     n_evals: int
     sweeps_done: int
     min_abs_margin: float  # smallest |gain - tau*max(|f|,1e-30)| over all decisions
-    margins: Optional[np.ndarray] = None
+    margins: Optional[list] = None  # FIRST mode: (sweep, position, margin, f before) per decision
 
 
 def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
@@ -220,7 +220,7 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
                 margin = improvement(ev.f, f, p.obj_kind) - tau * max(abs(f), 1e-30)
                 min_margin = min(min_margin, abs(margin))
                 if keep_margins:
-                    margins.append(margin)
+                    margins.append((s, t, margin, f))
                 if margin > 0:
                     b, f, cur = b2, ev.f, ev
                     accepted.append((s, t, int(k), f))
@@ -243,5 +243,4 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
         sweeps_done += 1
         if not any_accept or (max_evals is not None and n_evals >= max_evals):
             break
-    return DbsResult(accepted, b, f, cur.o, cur.S, n_evals, sweeps_done, float(min_margin),
-                     np.asarray(margins) if keep_margins else None)
+    return DbsResult(accepted, b, f, cur.o, cur.S, n_evals, sweeps_done, float(min_margin), margins)

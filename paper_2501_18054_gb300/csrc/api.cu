@@ -1,0 +1,296 @@
+// C ABI entry points (include/pngf.h): argument checks, workspace layout and
+// dispatch to the kernels of factor.cu and sweep.cu.  No entry point
+// allocates device memory; all scratch is carved from the caller's workspace.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pngf_internal.cuh"
+
+namespace pngf {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Layout make_layout(const pngf_config& cfg) {
+  Layout L{};
+  const size_t n = (size_t)cfg.n_d, n_o = (size_t)cfg.n_o;
+  const bool mixed = cfg.precision == PNGF_MIXED;
+  L.ldw = (int)align_up(n + 1, 8);
+  L.ldl = (int)align_up(n, 32);
+  L.ldt = (int)align_up(n, 8);
+  L.R = mixed ? cfg.delay_r : 0;
+  L.n_part = 1024;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t c = sizeof(c128);
+  L.W = take(n * L.ldw * c);
+  L.LU = take(n * L.ldw * c);
+  L.Wlo_re = take(mixed ? n * L.ldl * sizeof(float) : 0);
+  L.Wlo_im = take(mixed ? n * L.ldl * sizeof(float) : 0);
+  L.X = take(n * (size_t)L.R * c);
+  L.xa = take((size_t)L.R * c);
+  // contiguous state block: diag, e, T, v, b
+  L.diag = off;
+  off += align_up(n * c, 256);
+  L.e = off;
+  off += align_up(n * c, 256);
+  L.T = off;
+  off += align_up(n_o * L.ldt * c, 256);
+  L.v = off;
+  off += align_up(n * c, 256);
+  L.b = off;
+  off += align_up(n, 256);
+  L.state_bytes = off - L.diag;
+  L.pos_of = take(n * sizeof(int));
+  L.part = take((size_t)L.n_part * (2 * sizeof(long long) + 2 * sizeof(double) + kMaxPorts * c));
+  L.cbuf = take(n * c);
+  L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
+  L.ipiv = take(2 * n * sizeof(int));
+  L.snapW = take(mixed ? 2 * n * L.ldl * sizeof(float) : n * L.ldw * c);
+  L.snapState = take(L.state_bytes + sizeof(Control));
+  L.ctl = take(sizeof(Control));
+  L.total = off;
+  return L;
+}
+
+static pngf_status check_config(const pngf_config* cfg) {
+  if (!cfg) return PNGF_EINVAL;
+  if (cfg->n_d < 1 || cfg->n_d > 32768) return PNGF_EINVAL;
+  if (cfg->n_o < 1 || cfg->n_o > PNGF_MAX_PORTS) return PNGF_EINVAL;
+  if (cfg->precision != PNGF_FP64 && cfg->precision != PNGF_MIXED) return PNGF_EINVAL;
+  if (cfg->mode != PNGF_FIRST_IMPROVEMENT && cfg->mode != PNGF_BEST_IMPROVEMENT) return PNGF_EINVAL;
+  if (cfg->objective != PNGF_OBJ_MAX_WEIGHTED_POWER && cfg->objective != PNGF_OBJ_MIN_INSERTION_LOSS)
+    return PNGF_EINVAL;
+  if (cfg->refresh_k < 0) return PNGF_EINVAL;
+  if (cfg->precision == PNGF_MIXED) {
+    if (cfg->delay_r < 1 || cfg->delay_r > 128) return PNGF_EINVAL;
+    return PNGF_EINVAL;  // the mixed path is not built into this library yet
+  }
+  if (!(cfg->tau >= 0.0)) return PNGF_EINVAL;
+  return PNGF_OK;
+}
+
+}  // namespace pngf
+
+using namespace pngf;
+
+extern "C" {
+
+pngf_status pngf_workspace_size(const pngf_config* cfg, size_t* bytes) {
+  pngf_status st = check_config(cfg);
+  if (st != PNGF_OK) return st;
+  if (!bytes) return PNGF_EINVAL;
+  *bytes = make_layout(*cfg).total;
+  return PNGF_OK;
+}
+
+pngf_status pngf_create(const pngf_config* cfg, const double* G_dd, const double* G_od, const double* c_d,
+                        const double* c_o, const double* dv, void* workspace, size_t workspace_bytes,
+                        pngf_stream stream, pngf_ctx** out) {
+  if (!out) return PNGF_EINVAL;
+  *out = nullptr;
+  pngf_status st = check_config(cfg);
+  if (st != PNGF_OK) return st;
+  if (!G_dd || !G_od || !c_d || !c_o || !dv || !workspace) return PNGF_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return PNGF_EINVAL;
+  for (const void* p : {(const void*)G_dd, (const void*)G_od, (const void*)c_d, (const void*)c_o, (const void*)dv})
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return PNGF_EINVAL;
+  Layout L = make_layout(*cfg);
+  if (workspace_bytes < L.total) return PNGF_ENOMEM;
+  pngf_ctx* c = new (std::nothrow) pngf_ctx();
+  if (!c) return PNGF_ENOMEM;
+  c->cfg = *cfg;
+  c->L = L;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->G = reinterpret_cast<const c128*>(G_dd);
+  c->God = reinterpret_cast<const c128*>(G_od);
+  c->cd = reinterpret_cast<const c128*>(c_d);
+  c->co = reinterpret_cast<const c128*>(c_o);
+  c->dv = reinterpret_cast<const c128*>(dv);
+  c->ws = static_cast<char*>(workspace);
+  c->obj.n_o = cfg->n_o;
+  c->obj.kind = cfg->objective;
+  c->obj.tau = cfg->tau;
+  for (int p = 0; p < kMaxPorts; ++p) {
+    c->obj.w[p] = p < cfg->n_o ? cfg->obj_weights[p] : 0.0;
+    c->obj.off[p] = p < cfg->n_o ? mk(cfg->s_off[2 * p], cfg->s_off[2 * p + 1]) : mk(0.0, 0.0);
+    c->obj.scale[p] = p < cfg->n_o ? mk(cfg->s_scale[2 * p], cfg->s_scale[2 * p + 1]) : mk(0.0, 0.0);
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return PNGF_ECUDA;
+  }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  if (!coop) {
+    delete c;
+    return PNGF_ECUDA;
+  }
+  c->coop_ctas = sweep_grid_size(c);
+  Control* ctl = at<Control>(c, L.ctl);
+  if (cudaMemsetAsync(ctl, 0, sizeof(Control), c->stream) != cudaSuccess) {
+    delete c;
+    return PNGF_ECUDA;
+  }
+  *out = c;
+  return PNGF_OK;
+}
+
+pngf_status pngf_factor(pngf_ctx* c, const uint8_t* b) {
+  if (!c || !b) return PNGF_EINVAL;
+  pngf_status st = factor_fp64(c, b);
+  if (st == PNGF_OK) c->factored = true;
+  return st;
+}
+
+pngf_status pngf_score_flips(pngf_ctx* c, const int32_t* pixels, int32_t n, double* f_new, double* o_new) {
+  if (!c || n < 0 || (n > 0 && (!pixels || !f_new))) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  return score_flips(c, pixels, n, f_new, o_new);
+}
+
+pngf_status pngf_accept_flip(pngf_ctx* c, int32_t pixel) {
+  if (!c || pixel < 0 || pixel >= c->cfg.n_d) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  return accept_flip(c, pixel);
+}
+
+pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, int32_t* trace,
+                           double* trace_f, int32_t trace_cap, int64_t* counters) {
+  if (!c || n_sweeps < 0 || trace_cap < 0) return PNGF_EINVAL;
+  if (trace_cap > 0 && !trace && !trace_f) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  if (n_sweeps == 0) return PNGF_OK;
+  return run_sweep(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
+}
+
+pngf_status pngf_eval_ports(pngf_ctx* c, double* o_host, double* f_host) {
+  if (!c) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  Control h;
+  Control* ctl = at<Control>(c, c->L.ctl);
+  if (cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PNGF_ECUDA;
+  if (o_host)
+    for (int p = 0; p < c->cfg.n_o; ++p) {
+      o_host[2 * p] = h.o[p].x;
+      o_host[2 * p + 1] = h.o[p].y;
+    }
+  if (f_host) *f_host = h.f;
+  return h.status ? (pngf_status)h.status : PNGF_OK;
+}
+
+pngf_status pngf_get_design(pngf_ctx* c, uint8_t* b) {
+  if (!c || !b) return PNGF_EINVAL;
+  return cuda_status(cudaMemcpyAsync(b, at<uint8_t>(c, c->L.b), c->cfg.n_d, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+pngf_status pngf_get_state(pngf_ctx* c, double* W, double* diag_W, double* e, double* T, double* o) {
+  if (!c) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  const size_t n = c->cfg.n_d, n_o = c->cfg.n_o, cs = sizeof(c128);
+  cudaStream_t s = c->stream;
+  if (W) {
+    if (c->cfg.precision != PNGF_FP64) return PNGF_EINVAL;
+    if (cudaMemcpy2DAsync(W, n * cs, at<c128>(c, c->L.W), (size_t)c->L.ldw * cs, n * cs, n,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return PNGF_ECUDA;
+  }
+  if (diag_W && cudaMemcpyAsync(diag_W, at<c128>(c, c->L.diag), n * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  if (e && cudaMemcpyAsync(e, at<c128>(c, c->L.e), n * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  if (T && cudaMemcpy2DAsync(T, n * cs, at<c128>(c, c->L.T), (size_t)c->L.ldt * cs, n * cs, n_o,
+                             cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  if (o && cudaMemcpyAsync(o, &at<Control>(c, c->L.ctl)->o[0], n_o * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  return PNGF_OK;
+}
+
+pngf_status pngf_snapshot(pngf_ctx* c) {
+  if (!c) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  const Layout& L = c->L;
+  const size_t n = c->cfg.n_d;
+  cudaStream_t s = c->stream;
+  size_t wbytes = c->cfg.precision == PNGF_FP64 ? n * L.ldw * sizeof(c128) : 2 * n * L.ldl * sizeof(float);
+  size_t wsrc = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
+  if (cudaMemcpyAsync(c->ws + L.snapW, c->ws + wsrc, wbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws + L.snapState, c->ws + L.diag, L.state_bytes, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->ws + L.snapState + L.state_bytes, c->ws + L.ctl, sizeof(Control),
+                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  c->has_snapshot = true;
+  return PNGF_OK;
+}
+
+pngf_status pngf_restore(pngf_ctx* c) {
+  if (!c) return PNGF_EINVAL;
+  if (!c->has_snapshot) return PNGF_ENOTFACTORED;
+  const Layout& L = c->L;
+  const size_t n = c->cfg.n_d;
+  cudaStream_t s = c->stream;
+  size_t wbytes = c->cfg.precision == PNGF_FP64 ? n * L.ldw * sizeof(c128) : 2 * n * L.ldl * sizeof(float);
+  size_t wdst = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
+  // the control block is restored from its maintained fields on (f onwards): the
+  // latched status and the barrier words stay as they are
+  const size_t tail = offsetof(Control, f);
+  if (cudaMemcpyAsync(c->ws + wdst, c->ws + L.snapW, wbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws + L.diag, c->ws + L.snapState, L.state_bytes, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->ws + L.ctl + tail, c->ws + L.snapState + L.state_bytes + tail, sizeof(Control) - tail,
+                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  return PNGF_OK;
+}
+
+pngf_status pngf_get_phase_cycles(pngf_ctx* c, int64_t* host8) {
+  if (!c || !host8) return PNGF_EINVAL;
+  Control* ctl = at<Control>(c, c->L.ctl);
+  if (cudaMemcpyAsync(host8, ctl->phase_cycles, 8 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PNGF_ECUDA;
+  return PNGF_OK;
+}
+
+pngf_status pngf_sync(pngf_ctx* c) {
+  if (!c) return PNGF_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PNGF_ECUDA;
+  Control* ctl = at<Control>(c, c->L.ctl);
+  int st = 0;
+  if (cudaMemcpy(&st, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PNGF_ECUDA;
+  if (st) {
+    int zero = 0;
+    if (cudaMemcpy(&ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return PNGF_ECUDA;
+  }
+  return (pngf_status)st;
+}
+
+const char* pngf_status_string(pngf_status s) {
+  switch (s) {
+    case PNGF_OK: return "ok";
+    case PNGF_EINVAL: return "invalid argument";
+    case PNGF_ENOMEM: return "workspace too small";
+    case PNGF_ECUDA: return "CUDA runtime error";
+    case PNGF_ESINGULAR: return "singular system matrix (zero pivot)";
+    case PNGF_ENOTFACTORED: return "not factored";
+    case PNGF_ETIMEOUT: return "device wait timed out";
+    case PNGF_ENUMERIC: return "non-finite value";
+    case PNGF_ECAPACITY: return "trace buffer full";
+  }
+  return "unknown status";
+}
+
+void pngf_destroy(pngf_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,329 @@
+"""Thin ctypes binding of the C ABI in include/pngf.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and forwards
+plain integers / device pointers; all arithmetic of the hot path runs in the
+CUDA kernels of ``libpngf.so``.  ``DbsContext`` is a convenience wrapper that
+keeps the torch tensors (device memory) alive for one context.
+
+The library is loaded from this package directory; if it is missing the import
+of the binding functions fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpngf.so")
+
+PNGF_OK, PNGF_EINVAL, PNGF_ENOMEM, PNGF_ECUDA, PNGF_ESINGULAR = 0, 1, 2, 3, 4
+PNGF_ENOTFACTORED, PNGF_ETIMEOUT, PNGF_ENUMERIC, PNGF_ECAPACITY = 5, 6, 7, 8
+PNGF_FP64, PNGF_MIXED = 0, 1
+PNGF_FIRST_IMPROVEMENT, PNGF_BEST_IMPROVEMENT = 0, 1
+PNGF_OBJ_MAX_WEIGHTED_POWER, PNGF_OBJ_MIN_INSERTION_LOSS = 0, 1
+PNGF_MAX_PORTS = 8
+
+
+class pngf_config(ctypes.Structure):
+    _fields_ = [
+        ("n_d", ctypes.c_int32),
+        ("n_o", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("objective", ctypes.c_int32),
+        ("refresh_k", ctypes.c_int32),
+        ("delay_r", ctypes.c_int32),
+        ("n_ctas", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("obj_weights", ctypes.c_double * PNGF_MAX_PORTS),
+        ("s_off", ctypes.c_double * (2 * PNGF_MAX_PORTS)),
+        ("s_scale", ctypes.c_double * (2 * PNGF_MAX_PORTS)),
+    ]
+
+
+class PngfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {pngf_status_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpngf.so (built by ``paper_2501_18054_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_2501_18054_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        st = ctypes.c_int
+        sig = {
+            "pngf_workspace_size": (st, [ctypes.POINTER(pngf_config), ctypes.POINTER(ctypes.c_size_t)]),
+            "pngf_create": (st, [ctypes.POINTER(pngf_config), _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P,
+                                 ctypes.POINTER(_P)]),
+            "pngf_factor": (st, [_P, _P]),
+            "pngf_score_flips": (st, [_P, _P, ctypes.c_int32, _P, _P]),
+            "pngf_accept_flip": (st, [_P, ctypes.c_int32]),
+            "pngf_dbs_sweep": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]),
+            "pngf_eval_ports": (st, [_P, _P, _P]),
+            "pngf_get_design": (st, [_P, _P]),
+            "pngf_get_state": (st, [_P, _P, _P, _P, _P, _P]),
+            "pngf_snapshot": (st, [_P]),
+            "pngf_restore": (st, [_P]),
+            "pngf_sync": (st, [_P]),
+            "pngf_get_phase_cycles": (st, [_P, _P]),
+            "pngf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "pngf_destroy": (None, [_P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list:
+    """Names of the pngf_* entry points the loaded library resolves."""
+    L = lib()
+    names = []
+    for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
+              "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state", "pngf_snapshot",
+              "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
+        if hasattr(L, n):
+            names.append(n)
+    return names
+
+
+def _check(status: int, where: str) -> None:
+    if status != PNGF_OK:
+        raise PngfError(status, where)
+
+
+# ---------------------------------------------------------------- 1:1 entry points
+def pngf_status_string(status: int) -> str:
+    return lib().pngf_status_string(int(status)).decode()
+
+
+def pngf_workspace_size(cfg: pngf_config) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().pngf_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "pngf_workspace_size")
+    return int(out.value)
+
+
+def pngf_create(cfg: pngf_config, G_dd: int, G_od: int, c_d: int, c_o: int, dv: int, workspace: int,
+                workspace_bytes: int, stream: int) -> int:
+    h = _P()
+    _check(lib().pngf_create(ctypes.byref(cfg), G_dd, G_od, c_d, c_o, dv, workspace, workspace_bytes,
+                             stream, ctypes.byref(h)), "pngf_create")
+    return h.value
+
+
+def pngf_factor(ctx: int, b: int) -> None:
+    _check(lib().pngf_factor(ctx, b), "pngf_factor")
+
+
+def pngf_score_flips(ctx: int, pixels: int, n: int, f_new: int, o_new: Optional[int]) -> None:
+    _check(lib().pngf_score_flips(ctx, pixels, n, f_new, o_new), "pngf_score_flips")
+
+
+def pngf_accept_flip(ctx: int, pixel: int) -> None:
+    _check(lib().pngf_accept_flip(ctx, int(pixel)), "pngf_accept_flip")
+
+
+def pngf_dbs_sweep(ctx: int, n_sweeps: int, order: Optional[int], trace: Optional[int],
+                   trace_f: Optional[int], trace_cap: int, counters: Optional[int]) -> None:
+    _check(lib().pngf_dbs_sweep(ctx, n_sweeps, order, trace, trace_f, trace_cap, counters), "pngf_dbs_sweep")
+
+
+def pngf_eval_ports(ctx: int, n_o: int):
+    o = (ctypes.c_double * (2 * n_o))()
+    f = ctypes.c_double(0.0)
+    _check(lib().pngf_eval_ports(ctx, ctypes.cast(o, _P), ctypes.cast(ctypes.byref(f), _P)), "pngf_eval_ports")
+    arr = np.frombuffer(o, dtype=np.float64).copy()
+    return arr[0::2] + 1j * arr[1::2], float(f.value)
+
+
+def pngf_get_design(ctx: int, b: int) -> None:
+    _check(lib().pngf_get_design(ctx, b), "pngf_get_design")
+
+
+def pngf_get_state(ctx: int, W: Optional[int], diag_W: Optional[int], e: Optional[int], T: Optional[int],
+                   o: Optional[int]) -> None:
+    _check(lib().pngf_get_state(ctx, W, diag_W, e, T, o), "pngf_get_state")
+
+
+def pngf_snapshot(ctx: int) -> None:
+    _check(lib().pngf_snapshot(ctx), "pngf_snapshot")
+
+
+def pngf_restore(ctx: int) -> None:
+    _check(lib().pngf_restore(ctx), "pngf_restore")
+
+
+def pngf_get_phase_cycles(ctx: int) -> np.ndarray:
+    out = (ctypes.c_int64 * 8)()
+    _check(lib().pngf_get_phase_cycles(ctx, ctypes.cast(out, _P)), "pngf_get_phase_cycles")
+    return np.frombuffer(out, dtype=np.int64).copy()
+
+
+def pngf_sync(ctx: int) -> int:
+    return int(lib().pngf_sync(ctx))
+
+
+def pngf_destroy(ctx: int) -> None:
+    lib().pngf_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+def make_config(n_d: int, n_o: int, *, precision: int = PNGF_FP64, mode: int = PNGF_FIRST_IMPROVEMENT,
+                objective: int = PNGF_OBJ_MAX_WEIGHTED_POWER, refresh_k: int = 64, delay_r: int = 64,
+                n_ctas: int = 0, tau: float = 1e-9, obj_weights=None, s_off=None, s_scale=None) -> pngf_config:
+    cfg = pngf_config()
+    cfg.n_d, cfg.n_o = int(n_d), int(n_o)
+    cfg.precision, cfg.mode, cfg.objective = int(precision), int(mode), int(objective)
+    cfg.refresh_k, cfg.delay_r, cfg.n_ctas, cfg.tau = int(refresh_k), int(delay_r), int(n_ctas), float(tau)
+    w = np.zeros(PNGF_MAX_PORTS)
+    if obj_weights is not None:
+        w[:n_o] = np.asarray(obj_weights, dtype=np.float64)[:n_o]
+    off = np.zeros(PNGF_MAX_PORTS, dtype=np.complex128)
+    sc = np.ones(PNGF_MAX_PORTS, dtype=np.complex128)
+    if s_off is not None:
+        off[:n_o] = np.asarray(s_off, dtype=np.complex128)[:n_o]
+    if s_scale is not None:
+        sc[:n_o] = np.asarray(s_scale, dtype=np.complex128)[:n_o]
+    for p in range(PNGF_MAX_PORTS):
+        cfg.obj_weights[p] = w[p]
+        cfg.s_off[2 * p], cfg.s_off[2 * p + 1] = off[p].real, off[p].imag
+        cfg.s_scale[2 * p], cfg.s_scale[2 * p + 1] = sc[p].real, sc[p].imag
+    return cfg
+
+
+class DbsContext:
+    """One design region on one GPU: owns the torch tensors behind the C context."""
+
+    def __init__(self, case, *, precision: int = PNGF_FP64, mode: int = PNGF_FIRST_IMPROVEMENT,
+                 tau: float = 1e-9, refresh_k: int = 64, delay_r: int = 64, n_ctas: int = 0,
+                 device: str = "cuda", stream=None, inputs_on_device=None):
+        import torch
+
+        self.torch = torch
+        self.n_d, self.n_o = case.n_d, case.n_o
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+
+        def dev(x):
+            t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+            return t.to(self.device, dtype=torch.complex128).contiguous()
+
+        if inputs_on_device is not None:
+            self.G, self.God, self.cd, self.co, self.dv = inputs_on_device
+        else:
+            self.G, self.God, self.cd, self.co, self.dv = (dev(case.G_dd), dev(case.G_od), dev(case.c_d),
+                                                           dev(case.c_o), dev(case.dv))
+        self.cfg = make_config(case.n_d, case.n_o, precision=precision, mode=mode, objective=case.obj_kind,
+                               refresh_k=refresh_k, delay_r=delay_r, n_ctas=n_ctas, tau=tau,
+                               obj_weights=case.obj_weights, s_off=case.s_off, s_scale=case.s_scale)
+        self.ws_bytes = pngf_workspace_size(self.cfg)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.ctx = pngf_create(self.cfg, self.G.data_ptr(), self.God.data_ptr(), self.cd.data_ptr(),
+                               self.co.data_ptr(), self.dv.data_ptr(), self.ws.data_ptr(), self.ws_bytes,
+                               self.stream.cuda_stream)
+        self.counters = torch.zeros(8, dtype=torch.int64, device=self.device)
+
+    # -- calls
+    def factor(self, b) -> None:
+        bt = self.torch.as_tensor(np.asarray(b, dtype=np.uint8)).to(self.device) if not isinstance(
+            b, self.torch.Tensor) else b.to(self.device, self.torch.uint8)
+        self._b_keep = bt
+        pngf_factor(self.ctx, bt.data_ptr())
+
+    def score_flips(self, pixels, want_ports: bool = False):
+        torch = self.torch
+        px = torch.as_tensor(np.asarray(pixels, dtype=np.int32)).to(self.device)
+        f = torch.empty(len(px), dtype=torch.float64, device=self.device)
+        o = torch.empty((len(px), self.n_o), dtype=torch.complex128, device=self.device) if want_ports else None
+        pngf_score_flips(self.ctx, px.data_ptr(), len(px), f.data_ptr(), o.data_ptr() if o is not None else None)
+        self.stream.synchronize()
+        return (f.cpu().numpy(), o.cpu().numpy()) if want_ports else f.cpu().numpy()
+
+    def accept_flip(self, pixel: int) -> None:
+        pngf_accept_flip(self.ctx, pixel)
+
+    def dbs_sweep(self, n_sweeps: int, order=None, trace_cap: Optional[int] = None, sync: bool = True):
+        torch = self.torch
+        if trace_cap is None:
+            trace_cap = max(1, n_sweeps * self.n_d)
+        od = None
+        if order is not None:
+            od = order if isinstance(order, torch.Tensor) else torch.as_tensor(
+                np.ascontiguousarray(order, dtype=np.int32))
+            od = od.to(self.device, torch.int32).contiguous()
+        self._order_keep = od
+        self.trace = torch.zeros((trace_cap, 4), dtype=torch.int32, device=self.device)
+        self.trace_f = torch.zeros(trace_cap, dtype=torch.float64, device=self.device)
+        pngf_dbs_sweep(self.ctx, n_sweeps, od.data_ptr() if od is not None else None, self.trace.data_ptr(),
+                       self.trace_f.data_ptr(), trace_cap, self.counters.data_ptr())
+        if not sync:
+            return None
+        st = pngf_sync(self.ctx)
+        if st not in (PNGF_OK,):
+            raise PngfError(st, "pngf_dbs_sweep")
+        c = self.counters.cpu().numpy()
+        n_acc = int(min(c[0], trace_cap))
+        return dict(trace=self.trace[:n_acc].cpu().numpy(), trace_f=self.trace_f[:n_acc].cpu().numpy(),
+                    counters=c)
+
+    def eval_ports(self):
+        return pngf_eval_ports(self.ctx, self.n_o)
+
+    def design(self) -> np.ndarray:
+        b = self.torch.empty(self.n_d, dtype=self.torch.uint8, device=self.device)
+        pngf_get_design(self.ctx, b.data_ptr())
+        self.stream.synchronize()
+        return b.cpu().numpy()
+
+    def state(self, with_W: bool = False) -> dict:
+        torch = self.torch
+        n, n_o = self.n_d, self.n_o
+        W = torch.empty((n, n), dtype=torch.complex128, device=self.device) if with_W else None
+        d = torch.empty(n, dtype=torch.complex128, device=self.device)
+        e = torch.empty(n, dtype=torch.complex128, device=self.device)
+        T = torch.empty((n_o, n), dtype=torch.complex128, device=self.device)
+        o = torch.empty(n_o, dtype=torch.complex128, device=self.device)
+        pngf_get_state(self.ctx, W.data_ptr() if W is not None else None, d.data_ptr(), e.data_ptr(),
+                       T.data_ptr(), o.data_ptr())
+        self.stream.synchronize()
+        out = dict(diag=d.cpu().numpy(), e=e.cpu().numpy(), T=T.cpu().numpy(), o=o.cpu().numpy())
+        if W is not None:
+            out["W"] = W.cpu().numpy()
+        return out
+
+    def phase_cycles(self) -> np.ndarray:
+        return pngf_get_phase_cycles(self.ctx)
+
+    def snapshot(self) -> None:
+        pngf_snapshot(self.ctx)
+
+    def restore(self) -> None:
+        pngf_restore(self.ctx)
+
+    def sync(self) -> int:
+        return pngf_sync(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            pngf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
