@@ -39,7 +39,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--delay-r", type=int, default=64)
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--refresh-k", type=int, default=64)
     ap.add_argument("--tau", type=float, default=1e-9)
@@ -219,8 +221,8 @@ def main():
     prec = P.PNGF_MIXED if args.precision == "mixed" else P.PNGF_FP64
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        ctx = P.DbsContext(case, precision=prec, tau=args.tau, refresh_k=args.refresh_k, device=str(dev),
-                           stream=stream)
+        ctx = P.DbsContext(case, precision=prec, tau=args.tau, refresh_k=args.refresh_k, delay_r=args.delay_r,
+                           device=str(dev), stream=stream)
         b0 = Wl.random_design(n, seed=dist.rank)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -288,20 +290,39 @@ def main():
         value = total_evals / (ms_max / 1e3)
         kms = [a.elapsed_time(b) for a, b in kev]
         k_avg = sum(kms) / len(kms)
-        # algorithmic work of the dominant kernel (persistent DBS sweep, FP64 path):
-        # per kept flip the rank-1 update of the upper triangle, 4 DFMA = 8 flop per element
-        tri = n * (n + 1) / 2
-        flops = acc_per_step * 8.0 * tri
-        bytes_w = acc_per_step * 32.0 * tri
-        achieved_gflops = flops / (k_avg / 1e3) / 1e9
         peaks = measured_peaks()
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-        roofline = {"bound": "alu", "achieved": achieved_gflops / 1e3, "peak": peak_fp64 / 1e3,
-                    "unit": "TFLOP/s", "frac": achieved_gflops / peak_fp64,
-                    "traffic": None, "kernel": "dbs_fp64_kernel",
-                    "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks (152 SMs x 2 DFMA/clk)",
-                    "hbm_view": {"achieved_gbs": bytes_w / (k_avg / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                                 "frac": bytes_w / (k_avg / 1e3) / 1e9 / hbm_peak, "peak_source": "measured"}}
+        tri = n * (n + 1) / 2
+        if prec == P.PNGF_FP64:
+            # dominant kernel: the persistent FP64 DBS sweep.  Algorithmic work per
+            # launch: the rank-1 update of the upper triangle of W per kept flip,
+            # 4 DFMA = 8 flop per complex element (32 bytes of W read + written).
+            flops = acc_per_step * 8.0 * tri
+            bytes_w = acc_per_step * 32.0 * tri
+            achieved_gflops = flops / (k_avg / 1e3) / 1e9
+            roofline = {"bound": "alu", "achieved": achieved_gflops / 1e3, "peak": peak_fp64 / 1e3,
+                        "unit": "TFLOP/s", "frac": achieved_gflops / peak_fp64, "traffic": None,
+                        "kernel": "dbs_fp64_kernel",
+                        "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks "
+                                       "(152 SMs x 2 DFMA/clk x 2 flop x clock)",
+                        "hbm_view": {"achieved_gbs": bytes_w / (k_avg / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                                     "frac": bytes_w / (k_avg / 1e3) / 1e9 / hbm_peak,
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
+        else:
+            # dominant kernel: the persistent mixed DBS sweep.  Algorithmic HBM bytes per
+            # launch: per flush the upper triangle of the two FP32 planes read + written
+            # (16 B per element), per refresh one read of G (16 B) and of the FP32
+            # upper triangle (8 B), per kept flip one column of the FP32 planes (8 B x n),
+            # per evaluation (3 + n_o) x 16 B of FP64 state.
+            n_flush, n_ref = int(c2[5]), int(c2[4])
+            bytes_alg = (n_flush * 16.0 * tri + n_ref * (16.0 * n * n + 8.0 * tri) + acc_per_step * 8.0 * n
+                         + evals_per_step * (3 + n_o) * 16.0)
+            gbs = bytes_alg / (k_avg / 1e3) / 1e9
+            roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "traffic": None, "kernel": "dbs_mixed_kernel",
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
+                        "note": "one kept flip at a time: the single-run search is latency-bound "
+                                "(grid barrier + selection per kept flip); see phase_ms_cta0"}
         # ---- end to end through the C ABI with host buffers
         e2e = None
         if not args.no_e2e:
@@ -328,6 +349,64 @@ def main():
             e2e_s = dist.max(torch, w1 - w0, dev)
             e2e = {"value": total_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)}
+        # ---- the same run on the FP64 path (same GPU, same start) for the speedup and
+        #      the S-parameter error of the mixed path
+        compare = None
+        restore_and_run = step
+        restore_and_run()
+        stream.synchronize()
+        o_main, f_main = ctx.eval_ports()
+        b_main = ctx.design()
+        trace_main = trace[:min(acc_per_step, trace_cap), 2].cpu().numpy().copy()
+        if prec == P.PNGF_MIXED and not args.no_fp64_compare:
+            ref = P.DbsContext(case, precision=P.PNGF_FP64, tau=args.tau, refresh_k=args.refresh_k, device=str(dev),
+                               stream=stream, inputs_on_device=(ctx.G, ctx.God, ctx.cd, ctx.co, ctx.dv))
+            ref.factor(b0)
+            ref.snapshot()
+            cnt64 = torch.zeros(8, dtype=torch.int64, device=dev)
+            tr64 = torch.zeros((trace_cap, 4), dtype=torch.int32, device=dev)
+
+            def step64():
+                P.pngf_restore(ref.ctx)
+                P.pngf_dbs_sweep(ref.ctx, args.sweeps, None, tr64.data_ptr(), None, trace_cap, cnt64.data_ptr())
+
+            step64()
+            stream.synchronize()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            r0.record(stream)
+            for _ in range(reps):
+                step64()
+            r1.record(stream)
+            stream.synchronize()
+            if ref.sync() != 0:
+                raise RuntimeError("FP64 comparison run failed")
+            c64 = cnt64.cpu().numpy()
+            ms64 = r0.elapsed_time(r1) / reps
+            o64, f64 = ref.eval_ports()
+            b64 = ref.design()
+            k64 = tr64[:min(int(c64[0]), trace_cap), 2].cpu().numpy()
+            same = bool(np.array_equal(b64, b_main))
+            prefix = next((i for i, (x, y) in enumerate(zip(k64, trace_main)) if x != y), min(len(k64), len(trace_main)))
+            S_main = (o_main - case.s_off) * case.s_scale
+            S_64 = (o64 - case.s_off) * case.s_scale
+            compare = {"fp64_evals_per_s": float(c64[1]) / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                       "speedup_vs_fp64": (float(c64[1]) / (ms64 / 1e3)) and value / (float(c64[1]) / (ms64 / 1e3)),
+                       "same_final_design": same, "identical_accept_prefix": int(prefix),
+                       "accepts_fp64": int(c64[0]), "accepts_mixed": int(acc_per_step)}
+            if same:
+                compare["s_param_max_rel_err_vs_fp64"] = float(
+                    np.max(np.abs(S_main - S_64) / np.maximum(np.abs(S_64), 1e-3)))
+            ref.close()
+        if dist.rank == 0:
+            import oracle as O
+            ev = O.evaluate(O.Problem.from_case(case), b_main)
+            S_exact = (ev.o - case.s_off) * case.s_scale
+            S_main = (o_main - case.s_off) * case.s_scale
+            compare = dict(compare or {})
+            compare["s_param_max_rel_err_vs_oracle"] = float(
+                np.max(np.abs(S_main - S_exact) / np.maximum(np.abs(S_exact), 1e-3)))
+            compare["s_param_err_note"] = "final design of the timed run, exact S from the CPU FP64 oracle"
         cpu = None
         if dist.rank == 0 and not args.no_cpu_baseline:
             v, m, dt = time_oracle(case, b0, args.cpu_sample_evals)
@@ -342,6 +421,7 @@ def main():
             config={"workload": args.workload, "n_d": n, "n_o": n_o, "precision": args.precision,
                     "mode": "first-improvement, raster order", "max_sweeps": args.sweeps,
                     "refresh_k": args.refresh_k, "tau": args.tau,
+                    "delay_r": args.delay_r if prec == P.PNGF_MIXED else None,
                     "step": "restore factored start state + DBS run to convergence",
                     "l2": "inputs larger than L2 (W = %.0f MB complex128)" % (n * n * 16 / 1e6),
                     "replicas": "one independent run per GPU (seed = rank)"},
@@ -349,7 +429,8 @@ def main():
             evals_per_step=evals_per_step, accepts_per_step=acc_per_step, sweeps_per_step=sweeps_per_step,
             accepts_per_s=acc_per_step * args.steps / (ms_max / 1e3),
             sweeps_per_s=sweeps_per_step * args.steps / (ms_max / 1e3),
-            kernel_ms_avg=k_avg, factor_ms=factor_ms, fp64_peak_gflops=peak_fp64, phase_ms_cta0=phase_ms)
+            kernel_ms_avg=k_avg, factor_ms=factor_ms, fp64_peak_gflops=peak_fp64, phase_ms_cta0=phase_ms,
+            mixed_vs_fp64=compare)
         print(json.dumps(line))
     ctx.close()
     return 0

@@ -30,10 +30,13 @@ Layout make_layout(const pngf_config& cfg) {
   const size_t c = sizeof(c128);
   L.W = take(n * L.ldw * c);
   L.LU = take(n * L.ldw * c);
-  L.Wlo_re = take(mixed ? n * L.ldl * sizeof(float) : 0);
-  L.Wlo_im = take(mixed ? n * L.ldl * sizeof(float) : 0);
+  // mixed path: [Wlo_re | Wlo_im | X | xa] contiguous, so one copy snapshots them
+  const size_t plane = n * L.ldl * sizeof(float);
+  L.Wlo_re = take(mixed ? 2 * plane : 0);
+  L.Wlo_im = L.Wlo_re + (mixed ? plane : 0);
   L.X = take(n * (size_t)L.R * c);
   L.xa = take((size_t)L.R * c);
+  L.snapW_bytes = mixed ? off - L.Wlo_re : n * L.ldw * c;
   // contiguous state block: diag, e, T, v, b
   L.diag = off;
   off += align_up(n * c, 256);
@@ -48,10 +51,11 @@ Layout make_layout(const pngf_config& cfg) {
   L.state_bytes = off - L.diag;
   L.pos_of = take(n * sizeof(int));
   L.part = take((size_t)L.n_part * (2 * sizeof(long long) + 2 * sizeof(double) + kMaxPorts * c));
+  L.rec = take((size_t)2 * L.n_part * 256);
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
   L.ipiv = take(2 * n * sizeof(int));
-  L.snapW = take(mixed ? 2 * n * L.ldl * sizeof(float) : n * L.ldw * c);
+  L.snapW = take(L.snapW_bytes);
   L.snapState = take(L.state_bytes + sizeof(Control));
   L.ctl = take(sizeof(Control));
   L.total = off;
@@ -69,7 +73,7 @@ static pngf_status check_config(const pngf_config* cfg) {
   if (cfg->refresh_k < 0) return PNGF_EINVAL;
   if (cfg->precision == PNGF_MIXED) {
     if (cfg->delay_r < 1 || cfg->delay_r > 128) return PNGF_EINVAL;
-    return PNGF_EINVAL;  // the mixed path is not built into this library yet
+    if (cfg->refresh_k % cfg->delay_r != 0) return PNGF_EINVAL;  // refresh right after a flush
   }
   if (!(cfg->tau >= 0.0)) return PNGF_EINVAL;
   return PNGF_OK;
@@ -145,6 +149,7 @@ pngf_status pngf_create(const pngf_config* cfg, const double* G_dd, const double
 pngf_status pngf_factor(pngf_ctx* c, const uint8_t* b) {
   if (!c || !b) return PNGF_EINVAL;
   pngf_status st = factor_fp64(c, b);
+  if (st == PNGF_OK && c->cfg.precision == PNGF_MIXED) st = mixed_after_factor(c);
   if (st == PNGF_OK) c->factored = true;
   return st;
 }
@@ -158,7 +163,7 @@ pngf_status pngf_score_flips(pngf_ctx* c, const int32_t* pixels, int32_t n, doub
 pngf_status pngf_accept_flip(pngf_ctx* c, int32_t pixel) {
   if (!c || pixel < 0 || pixel >= c->cfg.n_d) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
-  return accept_flip(c, pixel);
+  return c->cfg.precision == PNGF_MIXED ? accept_flip_mixed(c, pixel) : accept_flip(c, pixel);
 }
 
 pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, int32_t* trace,
@@ -167,6 +172,7 @@ pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, 
   if (trace_cap > 0 && !trace && !trace_f) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
   if (n_sweeps == 0) return PNGF_OK;
+  if (c->cfg.precision == PNGF_MIXED) return run_sweep_mixed(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
   return run_sweep(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
 }
 
@@ -219,9 +225,9 @@ pngf_status pngf_snapshot(pngf_ctx* c) {
   if (!c) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
   const Layout& L = c->L;
-  const size_t n = c->cfg.n_d;
+
   cudaStream_t s = c->stream;
-  size_t wbytes = c->cfg.precision == PNGF_FP64 ? n * L.ldw * sizeof(c128) : 2 * n * L.ldl * sizeof(float);
+  size_t wbytes = L.snapW_bytes;
   size_t wsrc = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
   if (cudaMemcpyAsync(c->ws + L.snapW, c->ws + wsrc, wbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->ws + L.snapState, c->ws + L.diag, L.state_bytes, cudaMemcpyDeviceToDevice, s) !=
@@ -237,9 +243,9 @@ pngf_status pngf_restore(pngf_ctx* c) {
   if (!c) return PNGF_EINVAL;
   if (!c->has_snapshot) return PNGF_ENOTFACTORED;
   const Layout& L = c->L;
-  const size_t n = c->cfg.n_d;
+
   cudaStream_t s = c->stream;
-  size_t wbytes = c->cfg.precision == PNGF_FP64 ? n * L.ldw * sizeof(c128) : 2 * n * L.ldl * sizeof(float);
+  size_t wbytes = L.snapW_bytes;
   size_t wdst = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
   // the control block is restored from its maintained fields on (f onwards): the
   // latched status and the barrier words stay as they are

@@ -115,8 +115,9 @@ __device__ __forceinline__ void latch_status(Control* ctl, int s) {
 
 // ---------------------------------------------------------------- context
 struct Layout {
-  size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, cbuf, ipiv, rbuf,
+  size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, cbuf, ipiv, rbuf,
       snapW, snapState, ctl, total;
+  size_t snapW_bytes;  // bytes of the maintained inverse copied by snapshot
   int ldw, ldl, ldt, R, n_part;
   size_t state_bytes;  // contiguous state block [diag .. b] copied by snapshot
 };
@@ -152,6 +153,11 @@ __host__ __forceinline__ T* at(pngf_ctx* c, size_t off) {
 
 // factor.cu
 pngf_status factor_fp64(pngf_ctx* c, const uint8_t* b);
+// sweep_mixed.cu
+pngf_status mixed_after_factor(pngf_ctx* c);
+pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace,
+                            double* trace_f, int32_t trace_cap, int64_t* counters);
+pngf_status accept_flip_mixed(pngf_ctx* c, int pixel);
 // sweep.cu
 pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace,
                       double* trace_f, int32_t trace_cap, int64_t* counters);

@@ -1,0 +1,484 @@
+// Device building blocks shared by the FP64 and mixed-precision DBS kernels
+// (scoring, selection, pivot, state update, grid barrier, FP64 refresh).
+// Included by sweep.cu and sweep_mixed.cu; everything has internal linkage.
+#pragma once
+
+#include "pngf_internal.cuh"
+
+namespace pngf {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr unsigned long long kSpinLimit = 1ull << 24;  // ~seconds with the 128 ns back-off
+
+struct SweepArgs {
+  int n, n_o, ldw, ldt;
+  int mode, n_sweeps, trace_cap, refresh_k;
+  const int* order;
+  c128* W;
+  c128* diag;
+  c128* e;
+  c128* T;
+  c128* v;
+  const c128* dv;
+  uint8_t* b;
+  int* pos_of;
+  long long* part_key;  // [2][P]
+  double* part_gain;    // [2][P]
+  c128* cbuf;           // n
+  c128* rbuf;           // (1 + n_o) x n
+  c128* opart;          // P x n_o
+  Control* ctl;
+  int32_t* trace;
+  double* trace_f;
+  int64_t* counters;
+  const c128* G;
+  const c128* God;
+  const c128* cd;
+  const c128* co;
+  ObjParams op;
+  // mixed path
+  int mixed, ldl, R;
+  float* Wr;  // planar FP32 copy of W (upper triangle current)
+  float* Wi;
+  c128* X;    // n x R delayed columns c_i (row j holds c_0[j] .. c_{R-1}[j])
+  c128* xa;   // R coefficients alpha_i
+  void* rec;  // [2][P] candidate records
+};
+
+// a CTA's candidate of one scoring round, with the state the pivot needs
+struct CandRecord {
+  long long key;  // FIRST: visiting position; BEST: unused (see gain)
+  double gain;
+  int pixel;
+  int b;
+  c128 diag, e, dv;
+  c128 T[kMaxPorts];
+};
+
+// ---------------------------------------------------------------- grid barrier
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+__device__ bool grid_sync(Control* ctl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned g = ld_volatile(&ctl->bar_gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (ld_volatile(&ctl->bar_gen) == g) {
+        if (++it > kSpinLimit) {
+          latch_status(ctl, PNGF_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_ETIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- block reductions
+__device__ long long block_min_ll(long long x) {
+  __shared__ long long sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) x = min(x, __shfl_down_sync(0xffffffffu, x, off));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    x = lane < (int)(blockDim.x >> 5) ? sh[lane] : LLONG_MAX;
+    for (int off = 16; off > 0; off >>= 1) x = min(x, __shfl_down_sync(0xffffffffu, x, off));
+    if (lane == 0) sh[0] = x;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+// (gain, pixel): larger gain wins, ties -> lower pixel
+__device__ __forceinline__ bool better(double g1, int p1, double g2, int p2) {
+  return g1 > g2 || (g1 == g2 && p1 < p2);
+}
+
+__device__ void block_best(double& g, int& p) {
+  __shared__ double shg[kThreads / 32];
+  __shared__ int shp[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    double og = __shfl_down_sync(0xffffffffu, g, off);
+    int op = __shfl_down_sync(0xffffffffu, p, off);
+    if (better(og, op, g, p)) { g = og; p = op; }
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) { shg[w] = g; shp[w] = p; }
+  __syncthreads();
+  if (w == 0) {
+    g = lane < (int)(blockDim.x >> 5) ? shg[lane] : -INFINITY;
+    p = lane < (int)(blockDim.x >> 5) ? shp[lane] : INT_MAX;
+    for (int off = 16; off > 0; off >>= 1) {
+      double og = __shfl_down_sync(0xffffffffu, g, off);
+      int op = __shfl_down_sync(0xffffffffu, p, off);
+      if (better(og, op, g, p)) { g = og; p = op; }
+    }
+    if (lane == 0) { shg[0] = g; shp[0] = p; }
+  }
+  __syncthreads();
+  g = shg[0];
+  p = shp[0];
+}
+
+// ---------------------------------------------------------------- scoring
+// Candidate objective for flipping pixel j against the current state (Eq. 14).
+// Returns false for a numerically singular candidate (|d_j| < 1e-14).
+__device__ __forceinline__ bool score_pixel(const SweepArgs& a, const ObjParams& op, int j, const c128* o,
+                                            double& f_new, c128* o_new) {
+  c128 dvj = a.dv[j];
+  c128 delta = a.b[j] ? mk(-dvj.x, -dvj.y) : dvj;
+  c128 dj = csub(mk(1.0, 0.0), cmul(delta, a.diag[j]));
+  if (cabs2(dj) < 1e-28) return false;
+  c128 alpha = cdiv(delta, dj);
+  c128 coef = cmul(alpha, a.e[j]);
+  double fn = 0.0;
+#pragma unroll 1
+  for (int p = 0; p < a.n_o; ++p) {
+    c128 on = cfma(coef, a.T[(size_t)p * a.ldt + j], o[p]);
+    if (o_new) o_new[p] = on;
+    fn += objective_term(op, p, on);
+  }
+  f_new = fn;
+  return true;
+}
+
+// packed upper-triangle index -> (row, column); off(i) = i*n - i*(i-1)/2
+__device__ __forceinline__ void tri_rc(long long e, int n, int& i, int& j) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    long long off = (long long)mid * n - (long long)mid * (mid - 1) / 2;
+    if (off <= e) lo = mid; else hi = mid - 1;
+  }
+  i = lo;
+  j = lo + (int)(e - ((long long)lo * n - (long long)lo * (lo - 1) / 2));
+}
+
+// W += alpha c c^T on packed elements [eb, ee) of the upper triangle.
+// Thread t walks elements eb + t + m*blockDim; four consecutive steps of the
+// walk are issued together so that four independent loads are in flight.
+__device__ __forceinline__ void tri_step(int& i, int& j, int n, int stride) {
+  j += stride;
+  // carry into the following rows (row i+1 starts at column i+1); past the
+  // last row the walk is beyond ee and the caller stops
+  while (j >= n && i < n) {
+    j -= n;
+    ++i;
+    j += i;
+  }
+}
+
+__device__ void rank1_upper(c128* __restrict__ W, int n, int ldw, const c128* __restrict__ c, c128 alpha,
+                            long long eb, long long ee) {
+  long long e = eb + threadIdx.x;
+  if (e >= ee) return;
+  const int stride = blockDim.x;
+  int i0, j0;
+  tri_rc(e, n, i0, j0);
+  while (e + 3LL * stride < ee) {
+    int i1 = i0, j1 = j0;
+    tri_step(i1, j1, n, stride);
+    int i2 = i1, j2 = j1;
+    tri_step(i2, j2, n, stride);
+    int i3 = i2, j3 = j2;
+    tri_step(i3, j3, n, stride);
+    c128* p0 = W + (size_t)i0 * ldw + j0;
+    c128* p1 = W + (size_t)i1 * ldw + j1;
+    c128* p2 = W + (size_t)i2 * ldw + j2;
+    c128* p3 = W + (size_t)i3 * ldw + j3;
+    c128 w0 = *p0, w1 = *p1, w2 = *p2, w3 = *p3;
+    c128 c0 = c[j0], c1 = c[j1], c2 = c[j2], c3 = c[j3];
+    c128 a0 = cmul(alpha, c[i0]);
+    c128 a1 = (i1 == i0) ? a0 : cmul(alpha, c[i1]);
+    c128 a2 = (i2 == i1) ? a1 : cmul(alpha, c[i2]);
+    c128 a3 = (i3 == i2) ? a2 : cmul(alpha, c[i3]);
+    *p0 = cfma(a0, c0, w0);
+    *p1 = cfma(a1, c1, w1);
+    *p2 = cfma(a2, c2, w2);
+    *p3 = cfma(a3, c3, w3);
+    i0 = i3;
+    j0 = j3;
+    tri_step(i0, j0, n, stride);
+    e += 4LL * stride;
+  }
+  for (; e < ee; e += stride) {
+    c128* p = W + (size_t)i0 * ldw + j0;
+    *p = cfma(cmul(alpha, c[i0]), c[j0], *p);
+    tri_step(i0, j0, n, stride);
+  }
+}
+
+struct Pivot {
+  int k;
+  c128 alpha, coef;  // coef = alpha e_k
+  c128 Tk[kMaxPorts];
+};
+
+__device__ __forceinline__ void make_pivot(const SweepArgs& a, int k, Pivot& pv) {
+  c128 dvk = a.dv[k];
+  c128 delta = a.b[k] ? mk(-dvk.x, -dvk.y) : dvk;
+  c128 dk = csub(mk(1.0, 0.0), cmul(delta, a.diag[k]));
+  pv.k = k;
+  pv.alpha = cdiv(delta, dk);
+  pv.coef = cmul(pv.alpha, a.e[k]);
+  FOR_PORTS(p, a.n_o) pv.Tk[p] = a.T[(size_t)p * a.ldt + k];
+}
+
+// state update of pixels [pb, pe) given c = cbuf
+__device__ void update_state(const SweepArgs& a, const Pivot& pv, int pb, int pe) {
+  for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
+    c128 cj = a.cbuf[j];
+    c128 aj = cmul(pv.alpha, cj);
+    a.diag[j] = cfma(aj, cj, a.diag[j]);
+    a.e[j] = cfma(pv.coef, cj, a.e[j]);
+#pragma unroll 1
+    for (int p = 0; p < a.n_o; ++p) {
+      c128* t = a.T + (size_t)p * a.ldt + j;
+      *t = cfma(aj, pv.Tk[p], *t);
+    }
+    if (j == pv.k) {
+      uint8_t nb = a.b[j] ^ 1;
+      a.b[j] = nb;
+      a.v[j] = nb ? a.dv[j] : mk(0.0, 0.0);
+    }
+  }
+}
+
+// c_j = W[k][j] (j >= k) or W[j][k] (j < k) for j in [pb, pe)
+__device__ void gather_column(const SweepArgs& a, int k, int pb, int pe) {
+  for (int j = pb + threadIdx.x; j < pe; j += blockDim.x)
+    a.cbuf[j] = (j >= k) ? a.W[(size_t)k * a.ldw + j] : a.W[(size_t)j * a.ldw + k];
+}
+
+// ---------------------------------------------------------------- refresh
+// One FP64 iterative-refinement step of e and of the rows of T:
+//   e: r = c_d - (e - G (v.e)),         e += r + W (v.r)
+//   T: R = G_od - (T - (T diag v) G),   T += R + (R diag v) W      (G, W symmetric)
+// Scratch rbuf holds four blocks of nv = 1 + n_o vectors of length n:
+//   [0] residuals r, [1] x = v.[e, T], [2] x2 = v.r, [3] row sums of the upper triangle.
+__device__ __forceinline__ c128* rvec(const SweepArgs& a, int blk, int q) {
+  return a.rbuf + ((size_t)blk * (1 + a.n_o) + q) * a.n;
+}
+
+__device__ __forceinline__ c128 warp_sum(c128 v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// R0: x = v.[e, T] for own pixels
+__device__ void refresh_x(const SweepArgs& a, int pb, int pe) {
+  for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
+    c128 vj = a.v[j];
+    rvec(a, 1, 0)[j] = cmul(vj, a.e[j]);
+    for (int p = 0; p < a.n_o; ++p) rvec(a, 1, 1 + p)[j] = cmul(vj, a.T[(size_t)p * a.ldt + j]);
+  }
+}
+
+// R1: residuals of own rows (row j of G dotted with x), and x2 = v.r
+#define FOR_VECS(q, nv) _Pragma("unroll") for (int q = 0; q < 1 + kMaxPorts; ++q) if (q < (nv))
+__device__ __noinline__ void refresh_residual(const SweepArgs& a, int pb, int pe) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nv = 1 + a.n_o;
+  for (int j = pb + warp; j < pe; j += nw) {
+    const c128* g = a.G + (size_t)j * a.n;
+    c128 acc[1 + kMaxPorts];
+    FOR_VECS(q, nv) acc[q] = mk(0.0, 0.0);
+#pragma unroll 4
+    for (int i = lane; i < a.n; i += 32) {
+      c128 gi = g[i];
+      FOR_VECS(q, nv) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
+    }
+    FOR_VECS(q, nv) {
+      c128 sum = warp_sum(acc[q]);
+      if (lane == 0) {
+        c128 rhs = q == 0 ? a.cd[j] : a.God[(size_t)(q - 1) * a.n + j];
+        c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
+        c128 r = cadd(csub(rhs, y), sum);
+        rvec(a, 0, q)[j] = r;
+        rvec(a, 2, q)[j] = cmul(a.v[j], r);
+      }
+    }
+  }
+}
+
+// R2: corrections (I + W V) r for own rows, W symmetric with its upper
+// triangle current: row j takes sum_{i>=j} W[j][i] x2_i from its own row and
+// sum_{i<j} W[i][j] x2_i from the rows above (a strip of columns [pb, pe)).
+// The residual r is FP64; the product W x2 only has to be accurate relative
+// to |r| (classic mixed-precision iterative refinement), so it runs in FP32
+// arithmetic on the FP64-stored W and is added to r in FP64.
+struct f2c {
+  float x, y;
+};
+__device__ __forceinline__ f2c f2(c128 a) { return f2c{(float)a.x, (float)a.y}; }
+__device__ __forceinline__ f2c f2fma(f2c a, f2c b, f2c c) {
+  return f2c{fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y))};
+}
+__device__ __forceinline__ f2c f2sum(f2c v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// element (i, j) of the maintained W with i <= j, as FP32 (FP64 storage or the
+// planar FP32 copy of the mixed path)
+__device__ __forceinline__ f2c w_upper(const SweepArgs& a, int i, int j) {
+  if (a.mixed) {
+    size_t o = (size_t)i * a.ldl + j;
+    return f2c{a.Wr[o], a.Wi[o]};
+  }
+  return f2(a.W[(size_t)i * a.ldw + j]);
+}
+
+__device__ __noinline__ void refresh_correct(const SweepArgs& a, int pb, int pe) {
+  __shared__ f2c red[kThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nv = 1 + a.n_o;
+  // upper part, one warp per own row
+  for (int j = pb + warp; j < pe; j += nw) {
+    f2c acc[1 + kMaxPorts];
+    FOR_VECS(q, nv) acc[q] = f2c{0.f, 0.f};
+#pragma unroll 4
+    for (int i = j + lane; i < a.n; i += 32) {
+      f2c wi = w_upper(a, j, i);
+      FOR_VECS(q, nv) acc[q] = f2fma(wi, f2(rvec(a, 2, q)[i]), acc[q]);
+    }
+    FOR_VECS(q, nv) {
+      f2c sum = f2sum(acc[q]);
+      if (lane == 0) rvec(a, 3, q)[j] = mk(sum.x, sum.y);
+    }
+  }
+  __syncthreads();
+  // lower part: columns of this CTA in chunks of 32, rows above spread over warps
+  for (int c0 = pb; c0 < pe; c0 += 32) {
+    const int j = c0 + lane;
+    const int rows = min(pe, c0 + 32) - 1;  // rows i < j <= rows
+    f2c acc[1 + kMaxPorts];
+    FOR_VECS(q, nv) acc[q] = f2c{0.f, 0.f};
+#pragma unroll 4
+    for (int i = warp; i < rows; i += nw) {
+      if (i < j && j < pe) {
+        f2c wij = w_upper(a, i, j);
+        FOR_VECS(q, nv) acc[q] = f2fma(wij, f2(rvec(a, 2, q)[i]), acc[q]);
+      }
+    }
+    for (int q = 0; q < nv; ++q) {
+      f2c mine = f2c{0.f, 0.f};
+      FOR_VECS(qq, nv) if (qq == q) mine = acc[qq];
+      red[warp][lane] = mine;
+      __syncthreads();
+      if (warp == 0 && j < pe) {
+        double lx = 0.0, ly = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) {
+          lx += red[w2][lane].x;
+          ly += red[w2][lane].y;
+        }
+        c128 d = cadd(rvec(a, 0, q)[j], cadd(rvec(a, 3, q)[j], mk(lx, ly)));
+        if (q == 0) {
+          a.e[j] = cadd(a.e[j], d);
+        } else {
+          c128* t = a.T + (size_t)(q - 1) * a.ldt + j;
+          *t = cadd(*t, d);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// partial o sums of pixels [pb, pe) -> opart[cta]
+__device__ __noinline__ void ports_partial(const SweepArgs& a, int pb, int pe) {
+  __shared__ c128 red[kMaxPorts][kThreads / 32];
+  c128 acc[kMaxPorts];
+  FOR_PORTS(p, a.n_o) acc[p] = mk(0.0, 0.0);
+  for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
+    c128 ve = cmul(a.v[j], a.e[j]);
+    FOR_PORTS(p, a.n_o) acc[p] = cfma(a.God[(size_t)p * a.n + j], ve, acc[p]);
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FOR_PORTS(p, a.n_o) {
+    for (int off = 16; off > 0; off >>= 1) {
+      acc[p].x += __shfl_down_sync(0xffffffffu, acc[p].x, off);
+      acc[p].y += __shfl_down_sync(0xffffffffu, acc[p].y, off);
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    FOR_PORTS(p, a.n_o) red[p][w] = acc[p];
+  }
+  __syncthreads();
+  if (threadIdx.x < a.n_o) {
+    c128 s = mk(0.0, 0.0);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s = cadd(s, red[threadIdx.x][q]);
+    a.opart[(size_t)blockIdx.x * a.n_o + threadIdx.x] = s;
+  }
+}
+
+SweepArgs make_args(pngf_ctx* c) {
+  SweepArgs a{};
+  const Layout& L = c->L;
+  a.n = c->cfg.n_d;
+  a.n_o = c->cfg.n_o;
+  a.ldw = L.ldw;
+  a.ldt = L.ldt;
+  a.mode = c->cfg.mode;
+  a.refresh_k = c->cfg.refresh_k;
+  a.W = at<c128>(c, L.W);
+  a.diag = at<c128>(c, L.diag);
+  a.e = at<c128>(c, L.e);
+  a.T = at<c128>(c, L.T);
+  a.v = at<c128>(c, L.v);
+  a.dv = c->dv;
+  a.b = at<uint8_t>(c, L.b);
+  a.pos_of = at<int>(c, L.pos_of);
+  a.part_key = at<long long>(c, L.part);
+  a.part_gain = reinterpret_cast<double*>(a.part_key + 2 * L.n_part);
+  a.opart = reinterpret_cast<c128*>(a.part_gain + 2 * L.n_part);
+  a.cbuf = at<c128>(c, L.cbuf);
+  a.rbuf = at<c128>(c, L.rbuf);
+  a.ctl = at<Control>(c, L.ctl);
+  a.G = c->G;
+  a.God = c->God;
+  a.cd = c->cd;
+  a.co = c->co;
+  a.op = c->obj;
+  a.mixed = c->cfg.precision == PNGF_MIXED;
+  a.ldl = L.ldl;
+  a.R = L.R;
+  a.Wr = at<float>(c, L.Wlo_re);
+  a.Wi = at<float>(c, L.Wlo_im);
+  a.X = at<c128>(c, L.X);
+  a.xa = at<c128>(c, L.xa);
+  a.rec = c->ws + L.rec;
+  return a;
+}
+
+
+}  // namespace
+}  // namespace pngf

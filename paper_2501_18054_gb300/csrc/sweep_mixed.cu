@@ -1,0 +1,566 @@
+// Direct binary search on the device, mixed-precision path.
+//
+// The maintained inverse W = M^-1 G (the paper's C~^-1, Supplementary Note 4)
+// is kept as a planar FP32 copy W_lo plus a delayed FP64 rank-r correction:
+//   W = W_lo + sum_{i<r} alpha_i x_i x_i^T,   x_i = column of W at kept flip i.
+// Everything that decides a flip stays FP64: diag(W), e, T, o, the
+// Sherman-Morrison denominators d_k and alpha (Eqs. 9 and 14).  Per kept flip
+// of pixel k only the column c = W[:,k] is needed:
+//   c_j = W_lo(k, j) + sum_{i<r} (alpha_i x_i[k]) x_i[j]      (FP32 base + FP64 sum)
+// which updates diag(W), e and T in FP64 and is appended to the delayed set.
+// Every R kept flips the delayed set is folded into W_lo with one rank-R
+// product over the upper triangle (the paper's O(N_opt^2) update of
+// Supplementary Note 3, done once per R flips), and every refresh_k flips e
+// and T are refined in FP64 against G.
+//
+// Each CTA publishes its best candidate together with the pixel state the
+// pivot needs, so one grid barrier per kept flip suffices: nobody reads the
+// state arrays of the chosen pixel while its owner updates them.
+#include <cstdio>
+
+#include "sweep_common.cuh"
+
+namespace pngf {
+namespace {
+
+static_assert(sizeof(CandRecord) <= 256, "candidate record slot");
+constexpr int kMaxDelay = 128;
+
+__device__ __forceinline__ CandRecord* rec_at(const SweepArgs& a, int slot, int q) {
+  return reinterpret_cast<CandRecord*>(a.rec) + (size_t)slot * gridDim.x + q;
+}
+
+__device__ __forceinline__ void fill_record(const SweepArgs& a, CandRecord* r, int j, long long key,
+                                            double gain) {
+  r->key = key;
+  r->gain = gain;
+  r->pixel = j;
+  r->b = a.b[j];
+  r->diag = a.diag[j];
+  r->e = a.e[j];
+  r->dv = a.dv[j];
+  for (int p = 0; p < a.n_o; ++p) r->T[p] = a.T[(size_t)p * a.ldt + j];
+}
+
+__device__ __forceinline__ void pivot_from_record(const CandRecord& r, int n_o, Pivot& pv) {
+  c128 delta = r.b ? mk(-r.dv.x, -r.dv.y) : r.dv;
+  c128 dk = csub(mk(1.0, 0.0), cmul(delta, r.diag));
+  pv.k = r.pixel;
+  pv.alpha = cdiv(delta, dk);
+  pv.coef = cmul(pv.alpha, r.e);
+  for (int p = 0; p < n_o; ++p) pv.Tk[p] = r.T[p];
+}
+
+// W_lo(i, j) of the symmetric matrix through its upper triangle, promoted to FP64
+__device__ __forceinline__ c128 wlo_sym(const SweepArgs& a, int i, int j) {
+  int r = min(i, j), c = max(i, j);
+  size_t o = (size_t)r * a.ldl + c;
+  return mk((double)a.Wr[o], (double)a.Wi[o]);
+}
+
+// column assembly + state update for own pixels; appends c to the delayed set.
+// One warp per pixel: lanes split the delayed sum, a shuffle reduction adds it.
+__device__ void mixed_accept_own(const SweepArgs& a, const Pivot& pv, const c128* beta, int r, int pb, int pe) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = pb + warp; j < pe; j += nw) {
+    const c128* xj = a.X + (size_t)j * a.R;
+    c128 part = mk(0.0, 0.0);
+    for (int i = lane; i < r; i += 32) part = cfma(beta[i], xj[i], part);
+    for (int off = 16; off > 0; off >>= 1) {
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, off);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, off);
+    }
+    if (lane == 0) {
+      c128 cj = cadd(wlo_sym(a, pv.k, j), part);
+      a.X[(size_t)j * a.R + r] = cj;
+      c128 aj = cmul(pv.alpha, cj);
+      a.diag[j] = cfma(aj, cj, a.diag[j]);
+      a.e[j] = cfma(pv.coef, cj, a.e[j]);
+      for (int p = 0; p < a.n_o; ++p) {
+        c128* t = a.T + (size_t)p * a.ldt + j;
+        *t = cfma(aj, pv.Tk[p], *t);
+      }
+      if (j == pv.k) {
+        uint8_t nb = a.b[j] ^ 1;
+        a.b[j] = nb;
+        a.v[j] = nb ? a.dv[j] : mk(0.0, 0.0);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- flush
+// W_lo[I, J] += sum_{i<r} alpha_i x_i[I] x_i[J]^T over the upper triangle of
+// 64 x 64 tiles (diagonal tiles entirely).  FP32 operands in shared memory,
+// FP32 accumulation, added into the FP32 planes.
+constexpr int FT = 64;
+
+struct f2x {
+  float x, y;
+};
+
+__device__ void flush_tiles(const SweepArgs& a, int r, float* smem) {
+  const int n = a.n;
+  const int tn = (n + FT - 1) / FT;
+  const long long n_tiles = (long long)tn * (tn + 1) / 2;
+  f2x* Ys = reinterpret_cast<f2x*>(smem);          // [r][FT]   rows of tile I, times alpha
+  f2x* Xs = Ys + FT * kMaxDelay;                     // [r][FT]   rows of tile J
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 32 threads
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    int I, J;
+    tri_rc(t, tn, I, J);
+    const int i0 = I * FT, j0 = J * FT;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < FT * r; idx += blockDim.x) {
+      int rr = idx / r, q = idx % r;
+      int gi = i0 + rr, gj = j0 + rr;
+      c128 al = a.xa[q];
+      c128 xi = gi < n ? a.X[(size_t)gi * a.R + q] : mk(0.0, 0.0);
+      c128 xj = gj < n ? a.X[(size_t)gj * a.R + q] : mk(0.0, 0.0);
+      c128 yi = cmul(al, xi);
+      Ys[q * FT + rr] = f2x{(float)yi.x, (float)yi.y};
+      Xs[q * FT + rr] = f2x{(float)xj.x, (float)xj.y};
+    }
+    __syncthreads();
+    // thread (ty, tx) owns rows ty, ty+32 and columns tx, tx+16, tx+32, tx+48
+    float accr[2][4], acci[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) accr[u][v] = acci[u][v] = 0.f;
+    for (int q = 0; q < r; ++q) {
+      f2x y[2], x[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) y[u] = Ys[q * FT + ty + 32 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[v] = Xs[q * FT + tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          accr[u][v] = fmaf(y[u].x, x[v].x, fmaf(-y[u].y, x[v].y, accr[u][v]));
+          acci[u][v] = fmaf(y[u].x, x[v].y, fmaf(y[u].y, x[v].x, acci[u][v]));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int gi = i0 + ty + 32 * u;
+      if (gi >= n) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        int gj = j0 + tx + 16 * v;
+        if (gj >= n) continue;
+        size_t o = (size_t)gi * a.ldl + gj;
+        a.Wr[o] += accr[u][v];
+        a.Wi[o] += acci[u][v];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- persistent mixed DBS
+__global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
+  extern __shared__ float dyn_smem[];
+  const int P = gridDim.x, cta = blockIdx.x;
+  const int n = a.n;
+  const int pb = (int)((long long)n * cta / P), pe = (int)((long long)n * (cta + 1) / P);
+  Control* ctl = a.ctl;
+  __shared__ c128 s_o[kMaxPorts];
+  __shared__ double s_f;
+  __shared__ Pivot s_pv;
+  __shared__ int s_k, s_pos;
+  __shared__ ObjParams s_op;
+  __shared__ c128 s_beta[kMaxDelay];
+  if (threadIdx.x == 0) {
+    s_op = a.op;
+    FOR_PORTS(p, a.n_o) s_o[p] = ctl->o[p];
+    s_f = ctl->f;
+  }
+  __syncthreads();
+  long long n_acc = 0, n_evals = 0, n_refresh = 0, n_flush = 0;
+  int sweeps_done = 0, converged = 0, status = PNGF_OK;
+  int since_refresh = ctl->since_refresh;
+  int r = ctl->r_delay;
+  int s = 0, t = 0, acc_in_sweep = 0, slot = 0;
+  bool failed = false;
+  const bool timer = (cta == 0 && threadIdx.x == 0);
+  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long t_last = clock64(), t_begin = t_last;
+  auto tick = [&](int phase) {
+    if (timer) {
+      long long now = clock64();
+      ph[phase] += now - t_last;
+      t_last = now;
+    }
+  };
+  auto setup_sweep = [&](int sw) {
+    if (a.order)
+      for (int q = pb + threadIdx.x; q < pe; q += blockDim.x) {
+        int px = a.order[(size_t)sw * n + q];
+        if ((unsigned)px < (unsigned)n) a.pos_of[px] = q;
+        else latch_status(ctl, PNGF_EINVAL);
+      }
+  };
+  auto flush = [&]() -> bool {
+    if (!grid_sync(ctl)) return false;
+    flush_tiles(a, r, dyn_smem);
+    if (!grid_sync(ctl)) return false;
+    r = 0;
+    ++n_flush;
+    return true;
+  };
+  if (a.mode == PNGF_FIRST_IMPROVEMENT && a.order) {
+    setup_sweep(0);
+    if (!grid_sync(ctl)) failed = true;
+  }
+  const long long max_steps = a.n_sweeps;
+  while (!failed) {
+    const double f = s_f;
+    const double thr = accept_threshold(s_op, f);
+    // ---- score own pixels; the CTA's best candidate and its state go to a record
+    {
+      long long best = LLONG_MAX;
+      double g = -INFINITY;
+      int pix = INT_MAX;
+      for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
+        double fn;
+        if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+          int pos = a.order ? a.pos_of[j] : j;
+          if (pos < t) continue;
+          if (!score_pixel(a, s_op, j, s_o, fn, nullptr)) continue;
+          if (gain_of(s_op, fn, f) - thr > 0.0 && pos < best) { best = pos; pix = j; }
+        } else {
+          if (!score_pixel(a, s_op, j, s_o, fn, nullptr)) continue;
+          double gg = gain_of(s_op, fn, f);
+          if (better(gg, j, g, pix)) { g = gg; pix = j; }
+        }
+      }
+      CandRecord* rc = rec_at(a, slot, cta);
+      if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+        long long bmin = block_min_ll(best);
+        if (threadIdx.x == 0) a.part_key[slot * P + cta] = bmin;
+        if (bmin == LLONG_MAX) {
+          if (threadIdx.x == 0) rc->key = LLONG_MAX;
+        } else if (best == bmin) {
+          fill_record(a, rc, pix, best, 0.0);
+        }
+      } else {
+        double gb = g;
+        int pb2 = pix;
+        block_best(gb, pb2);
+        if (pb2 == INT_MAX) {
+          if (threadIdx.x == 0) { rc->key = LLONG_MAX; rc->gain = -INFINITY; rc->pixel = INT_MAX; }
+        } else if (pix == pb2) {
+          fill_record(a, rc, pix, 0, gb);
+        }
+      }
+    }
+    tick(0);
+    if (!grid_sync(ctl)) { failed = true; break; }
+    tick(1);
+    // ---- warp 0 picks the winning record; lane 0 forms the pivot
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      int win = -1;
+      if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+        long long best = LLONG_MAX;
+        int q_best = -1;
+        const long long* keys = a.part_key + slot * P;
+#pragma unroll 8
+        for (int q = lane; q < P; q += 32) {
+          long long kq = keys[q];
+          if (kq < best) { best = kq; q_best = q; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+          int oq = __shfl_xor_sync(0xffffffffu, q_best, off);
+          if (ob < best || (ob == best && oq < q_best)) { best = ob; q_best = oq; }
+        }
+        if (best != LLONG_MAX) win = q_best;
+      } else {
+        double g = -INFINITY;
+        int pix = INT_MAX, q_best = -1;
+        for (int q = lane; q < P; q += 32) {
+          const CandRecord* rq = rec_at(a, slot, q);
+          double gg = rq->gain;
+          int pp = rq->pixel;
+          if (pp != INT_MAX && better(gg, pp, g, pix)) { g = gg; pix = pp; q_best = q; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          double og = __shfl_xor_sync(0xffffffffu, g, off);
+          int op = __shfl_xor_sync(0xffffffffu, pix, off);
+          int oq = __shfl_xor_sync(0xffffffffu, q_best, off);
+          if (better(og, op, g, pix)) { g = og; pix = op; q_best = oq; }
+        }
+        if (q_best >= 0 && g - thr > 0.0) win = q_best;
+      }
+      if (lane == 0) {
+        s_k = -1;
+        s_pos = 0;
+        if (win >= 0) {
+          CandRecord rw = *rec_at(a, slot, win);
+          s_k = rw.pixel;
+          s_pos = (int)rw.key;
+          pivot_from_record(rw, a.n_o, s_pv);
+          FOR_PORTS(p, a.n_o) s_o[p] = cfma(s_pv.coef, s_pv.Tk[p], s_o[p]);
+          s_f = objective_of(s_op, s_o);
+        }
+      }
+    }
+    __syncthreads();
+    slot ^= 1;
+    const int k = s_k, pos_k = s_pos;
+    if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) {
+      status = PNGF_EINVAL;
+      break;
+    }
+    if (k < 0) {
+      if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+        n_evals += n - t;
+        ++sweeps_done;
+        if (acc_in_sweep == 0) { converged = 1; break; }
+        ++s;
+        if (s >= a.n_sweeps) break;
+        t = 0;
+        acc_in_sweep = 0;
+        if (a.order) {
+          setup_sweep(s);
+          if (!grid_sync(ctl)) { failed = true; break; }
+        }
+        tick(6);
+        continue;
+      } else {
+        n_evals += n;
+        ++sweeps_done;
+        converged = 1;
+        break;
+      }
+    }
+    // ---- keep the flip of pixel k
+    if (!isfinite(s_f)) status = PNGF_ENUMERIC;
+    if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+      n_evals += pos_k - t + 1;
+      t = pos_k + 1;
+    } else {
+      n_evals += n;
+      ++sweeps_done;
+    }
+    ++acc_in_sweep;
+    if (cta == 0 && threadIdx.x == 0) {
+      if (n_acc < a.trace_cap) {
+        if (a.trace) {
+          int32_t* tr = a.trace + 4 * n_acc;
+          tr[0] = a.mode == PNGF_FIRST_IMPROVEMENT ? s : (int)n_acc;
+          tr[1] = pos_k;
+          tr[2] = k;
+          tr[3] = 0;
+        }
+        if (a.trace_f) a.trace_f[n_acc] = s_f;
+      } else if (status == PNGF_OK) {
+        status = PNGF_ECAPACITY;
+      }
+      a.xa[r] = s_pv.alpha;
+    }
+    ++n_acc;
+    // beta_i = alpha_i x_i[k] for the delayed columns
+    for (int i = threadIdx.x; i < r; i += blockDim.x) s_beta[i] = cmul(a.xa[i], a.X[(size_t)k * a.R + i]);
+    __syncthreads();
+    tick(2);
+    mixed_accept_own(a, s_pv, s_beta, r, pb, pe);
+    ++r;
+    ++since_refresh;
+    __syncthreads();
+    tick(4);
+    if (r == a.R) {
+      if (!flush()) { failed = true; break; }
+      tick(3);
+      if (a.refresh_k > 0 && since_refresh >= a.refresh_k) {
+        since_refresh = 0;
+        ++n_refresh;
+        refresh_x(a, pb, pe);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        refresh_residual(a, pb, pe);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        refresh_correct(a, pb, pe);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        ports_partial(a, pb, pe);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        if (threadIdx.x == 0) {
+          FOR_PORTS(p, a.n_o) {
+            c128 acc = mk(0.0, 0.0);
+            for (int q = 0; q < P; ++q) acc = cadd(acc, a.opart[(size_t)q * a.n_o + p]);
+            s_o[p] = cadd(a.co[p], acc);
+          }
+          s_f = objective_of(s_op, s_o);
+        }
+        __syncthreads();
+        tick(5);
+      }
+    }
+    if (status == PNGF_ENUMERIC) break;
+    if (a.mode == PNGF_BEST_IMPROVEMENT && n_acc >= max_steps) break;
+    if (a.mode == PNGF_FIRST_IMPROVEMENT && t >= n) {
+      ++sweeps_done;
+      ++s;
+      if (s >= a.n_sweeps) break;
+      t = 0;
+      acc_in_sweep = 0;
+      if (a.order) {
+        if (!grid_sync(ctl)) { failed = true; break; }
+        setup_sweep(s);
+        if (!grid_sync(ctl)) { failed = true; break; }
+      }
+    }
+  }
+  if (cta == 0 && threadIdx.x == 0) {
+    if (failed) status = PNGF_ETIMEOUT;
+    FOR_PORTS(p, a.n_o) ctl->o[p] = s_o[p];
+    ctl->f = s_f;
+    ctl->since_refresh = since_refresh;
+    ctl->r_delay = r;
+    ctl->n_acc_total += (int)n_acc;
+    ctl->counters[0] = n_acc;
+    ctl->counters[1] = n_evals;
+    ctl->counters[2] = sweeps_done;
+    ctl->counters[3] = converged;
+    ctl->counters[4] = n_refresh;
+    ctl->counters[5] = n_flush;
+    ctl->counters[6] = status;
+    ctl->counters[7] = 0;
+    ph[7] = clock64() - t_begin;
+    for (int q = 0; q < 8; ++q) ctl->phase_cycles[q] = ph[q];
+    if (a.counters)
+      for (int q = 0; q < 8; ++q) a.counters[q] = ctl->counters[q];
+    if (status == PNGF_ENUMERIC || status == PNGF_ETIMEOUT || status == PNGF_EINVAL) latch_status(ctl, status);
+  }
+}
+
+// ---------------------------------------------------------------- after the factor
+__global__ void to_planar_fp32(const c128* __restrict__ W, int n, int ldw, float* __restrict__ Wr,
+                               float* __restrict__ Wi, int ldl) {
+  int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    c128 w = W[(size_t)i * ldw + j];
+    Wr[(size_t)i * ldl + j] = (float)w.x;
+    Wi[(size_t)i * ldl + j] = (float)w.y;
+  }
+}
+
+// ---------------------------------------------------------------- single calls
+__global__ void mixed_accept_kernel(SweepArgs a, int k) {
+  __shared__ Pivot s_pv;
+  __shared__ c128 s_beta[kMaxDelay];
+  __shared__ int s_r;
+  // every CTA rebuilds the pivot from the state of pixel k, which only the
+  // owner of k changes, after all CTAs have read it: pixel k's state is read
+  // from the snapshot written by accept_snapshot_kernel
+  const CandRecord* rk = reinterpret_cast<const CandRecord*>(a.rec);
+  if (threadIdx.x == 0) {
+    pivot_from_record(*rk, a.n_o, s_pv);
+    s_r = a.ctl->r_delay;
+  }
+  __syncthreads();
+  const int r = s_r;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) s_beta[i] = cmul(a.xa[i], a.X[(size_t)k * a.R + i]);
+  __syncthreads();
+  const int P = gridDim.x, n = a.n;
+  const int pb = (int)((long long)n * blockIdx.x / P), pe = (int)((long long)n * (blockIdx.x + 1) / P);
+  mixed_accept_own(a, s_pv, s_beta, r, pb, pe);
+}
+
+__global__ void accept_snapshot_kernel(SweepArgs a, int k) {
+  if (threadIdx.x == 0) {
+    CandRecord* rk = reinterpret_cast<CandRecord*>(a.rec);
+    fill_record(a, rk, k, 0, 0.0);
+    Pivot pv;
+    pivot_from_record(*rk, a.n_o, pv);
+    c128 o[kMaxPorts];
+    FOR_PORTS(p, a.n_o) o[p] = cfma(pv.coef, pv.Tk[p], a.ctl->o[p]);
+    FOR_PORTS(p, a.n_o) a.ctl->o[p] = o[p];
+    a.ctl->f = objective_of(a.op, o);
+    a.ctl->n_acc_total += 1;
+  }
+}
+
+__global__ void accept_finish_kernel(SweepArgs a) {
+  if (threadIdx.x == 0) {
+    const CandRecord* rk = reinterpret_cast<const CandRecord*>(a.rec);
+    Pivot pv;
+    pivot_from_record(*rk, a.n_o, pv);
+    int r = a.ctl->r_delay;
+    a.xa[r] = pv.alpha;
+    a.ctl->r_delay = r + 1;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) flush_kernel(SweepArgs a) {
+  extern __shared__ float dyn_smem[];
+  const int r = a.ctl->r_delay;
+  if (r < a.R) return;
+  flush_tiles(a, r, dyn_smem);
+}
+
+__global__ void flush_reset_kernel(SweepArgs a) {
+  if (threadIdx.x == 0 && a.ctl->r_delay >= a.R) a.ctl->r_delay = 0;
+}
+
+constexpr size_t kFlushSmem = 2 * FT * kMaxDelay * sizeof(f2x);
+
+}  // namespace
+
+pngf_status mixed_after_factor(pngf_ctx* c) {
+  const int n = c->cfg.n_d;
+  dim3 grid((n + 255) / 256 > 8 ? 8 : (n + 255) / 256, n);
+  to_planar_fp32<<<grid, 256, 0, c->stream>>>(at<c128>(c, c->L.W), n, c->L.ldw, at<float>(c, c->L.Wlo_re),
+                                                at<float>(c, c->L.Wlo_im), c->L.ldl);
+  return cuda_status(cudaGetLastError());
+}
+
+static int mixed_grid(pngf_ctx* c) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(dbs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
+    cudaFuncSetAttribute(flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
+    attr = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_mixed_kernel, kThreads, kFlushSmem);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2) per_sm = 2;
+  int g = c->n_sm * per_sm;
+  if (c->cfg.n_ctas > 0 && c->cfg.n_ctas < g) g = c->cfg.n_ctas;
+  if (g > c->L.n_part) g = c->L.n_part;
+  return g;
+}
+
+pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace, double* trace_f,
+                            int32_t trace_cap, int64_t* counters) {
+  SweepArgs a = make_args(c);
+  a.n_sweeps = n_sweeps;
+  a.order = order;
+  a.trace = trace;
+  a.trace_f = trace_f;
+  a.trace_cap = trace_cap;
+  a.counters = counters;
+  Control* ctl = a.ctl;
+  cudaError_t err = cudaMemsetAsync(&ctl->bar_count, 0, 2 * sizeof(unsigned), c->stream);
+  if (err != cudaSuccess) return PNGF_ECUDA;
+  int grid = mixed_grid(c);
+  void* params[] = {&a};
+  err = cudaLaunchCooperativeKernel((const void*)dbs_mixed_kernel, dim3(grid), dim3(kThreads), params, kFlushSmem,
+                                    c->stream);
+  return cuda_status(err);
+}
+
+pngf_status accept_flip_mixed(pngf_ctx* c, int pixel) {
+  SweepArgs a = make_args(c);
+  mixed_grid(c);
+  accept_snapshot_kernel<<<1, 32, 0, c->stream>>>(a, pixel);
+  mixed_accept_kernel<<<c->n_sm, kThreads, 0, c->stream>>>(a, pixel);
+  accept_finish_kernel<<<1, 32, 0, c->stream>>>(a);
+  flush_kernel<<<c->n_sm, kThreads, kFlushSmem, c->stream>>>(a);
+  flush_reset_kernel<<<1, 32, 0, c->stream>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace pngf

@@ -1,0 +1,158 @@
+"""Mixed-precision path (FP32 maintained inverse + FP64 decisions) through the C ABI.
+
+Bars:
+* right after the factor the scored state is FP64 (same as the FP64 path):
+  candidate objectives within 1e-9 of the oracle;
+* after kept flips the state follows the oracle's re-solves to FP32 accuracy
+  amplified by the conditioning (1e-5 relative on the dielectric cases);
+* DBS: when every oracle decision margin exceeds 1e-6 |f| (above the error of
+  a mixed-precision score: FP32 rounding 6e-8 of the maintained inverse,
+  amplified by the conditioning of M, ~1e-7 on these cases) the accepted
+  sequence equals the oracle's, and the final S-parameters agree within 1e-4
+  relative (the spec accuracy bar).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2501_18054_gb300 import workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2501_18054_gb300 import build as B
+    B.build()
+    from paper_2501_18054_gb300 import pngf
+    return pngf
+
+
+@pytest.fixture(scope="module")
+def fdfd64():
+    return W.get_case("fdfd64")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def s_rel(case, o, o_ref):
+    S = (np.asarray(o) - case.s_off) * case.s_scale
+    Sr = (np.asarray(o_ref) - case.s_off) * case.s_scale
+    return float(np.max(np.abs(S - Sr) / np.maximum(np.abs(Sr), 1e-3)))
+
+
+def _ctx(P, case, **kw):
+    kw.setdefault("precision", P.PNGF_MIXED)
+    return P.DbsContext(case, **kw)
+
+
+def test_mixed_factor_state_is_fp64(P, fdfd64):
+    case = fdfd64
+    b = W.random_design(case.n_d, 11)
+    ctx = _ctx(P, case, delay_r=8, refresh_k=16)
+    ctx.factor(b)
+    st = ctx.state()
+    v = case.dv * b
+    Wr = O.maintained_inverse(case.G_dd, v)
+    assert rel(st["diag"], np.diag(Wr)) < 1e-10
+    assert rel(st["T"], O.port_projection(case.G_dd, case.G_od, v)) < 1e-10
+    f_gpu = ctx.score_flips(np.arange(case.n_d))
+    f_ref = O.candidate_objectives(O.Problem.from_case(case), b, np.arange(case.n_d))
+    assert np.max(np.abs(f_gpu - f_ref) / np.abs(f_ref)) < 1e-9
+
+
+@pytest.mark.parametrize("n_accepts", [3, 8, 13])
+def test_mixed_accepts_follow_resolves(P, fdfd64, n_accepts):
+    """Standalone accepts across a flush (delay_r = 4)."""
+    case = fdfd64
+    b = W.random_design(case.n_d, 7)
+    ctx = _ctx(P, case, delay_r=4, refresh_k=0)
+    ctx.factor(b)
+    rng = np.random.default_rng(n_accepts)
+    for k in rng.choice(case.n_d, n_accepts, replace=False):
+        ctx.accept_flip(int(k))
+        b[k] ^= 1
+    st = ctx.state()
+    v = case.dv * b
+    Wr = O.maintained_inverse(case.G_dd, v)
+    ev = O.evaluate(O.Problem.from_case(case), b)
+    assert rel(st["diag"], np.diag(Wr)) < 1e-5
+    assert rel(st["e"], ev.e) < 1e-5
+    assert rel(st["T"], O.port_projection(case.G_dd, case.G_od, v)) < 1e-5
+    o, _ = ctx.eval_ports()
+    assert s_rel(case, o, ev.o) < 1e-5
+    assert np.array_equal(ctx.design(), b)
+    # the scores after the accepts agree with re-solves to FP32-level accuracy
+    f_gpu = ctx.score_flips(np.arange(0, case.n_d, 7))
+    f_ref = O.candidate_objectives(O.Problem.from_case(case), b, np.arange(0, case.n_d, 7))
+    assert np.max(np.abs(f_gpu - f_ref) / np.abs(f_ref)) < 1e-5
+
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", f"{name}.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("name", ["fdfd64_first_raster", "fdfd64_first_shuffled", "fdfd64_best"])
+@pytest.mark.parametrize("delay_r,refresh_k", [(4, 8), (16, 32), (64, 0)])
+def test_mixed_dbs_matches_oracle(P, fdfd64, name, delay_r, refresh_k):
+    g = _golden(name)
+    case = fdfd64
+    sp = g["spec"]
+    assert g["min_abs_margin"] > 1e-6 * abs(g["final_f"])  # decisions far from the score error
+    b0 = W.random_design(case.n_d, sp["seed"])
+    mode = P.PNGF_BEST_IMPROVEMENT if sp["mode"] == O.BEST_IMPROVEMENT else P.PNGF_FIRST_IMPROVEMENT
+    ctx = _ctx(P, case, mode=mode, tau=g["tau"], delay_r=delay_r, refresh_k=refresh_k)
+    ctx.factor(b0)
+    order = None if sp["order"] == "raster" else W.shuffled_order(case.n_d, sp["n_sweeps"], seed=sp["seed"])
+    res = ctx.dbs_sweep(sp["n_sweeps"], order=order)
+    ref_k = [k for _, _, k, _ in g["accepted"]]
+    assert [int(r[2]) for r in res["trace"]] == ref_k
+    assert np.array_equal(ctx.design(), np.array(g["final_b"], np.uint8))
+    o, _ = ctx.eval_ports()
+    o_ref = np.array([complex(*z) for z in g["final_o"]])
+    assert s_rel(case, o, o_ref) < 1e-4
+    c = res["counters"]
+    assert c[1] == g["n_evals"]
+    assert c[5] == len(ref_k) // delay_r  # flushes
+
+
+def test_mixed_restore_replays(P, fdfd64):
+    ctx = _ctx(P, fdfd64, delay_r=8, refresh_k=16)
+    ctx.factor(W.random_design(fdfd64.n_d, 0))
+    ctx.snapshot()
+    r1 = ctx.dbs_sweep(3)
+    ctx.restore()
+    r2 = ctx.dbs_sweep(3)
+    assert np.array_equal(r1["trace"], r2["trace"])
+    assert np.array_equal(r1["trace_f"], r2["trace_f"])
+
+
+def test_mixed_vs_fp64_full_size(P):
+    """N_d = 4096 (the bench workload): the mixed run against the FP64 run and
+    the oracle; S-parameters of the final design within 1e-4 relative."""
+    case = W.get_case("fdfd256")
+    b0 = W.random_design(case.n_d, 0)
+    f64 = P.DbsContext(case, precision=P.PNGF_FP64, refresh_k=64)
+    f64.factor(b0)
+    r64 = f64.dbs_sweep(10)
+    mix = _ctx(P, case, delay_r=64, refresh_k=64)
+    mix.factor(b0)
+    rmx = mix.dbs_sweep(10)
+    k64 = [int(r[2]) for r in r64["trace"]]
+    kmx = [int(r[2]) for r in rmx["trace"]]
+    n_same = next((i for i, (x, y) in enumerate(zip(k64, kmx)) if x != y), min(len(k64), len(kmx)))
+    print(f"fp64 accepts {len(k64)}, mixed {len(kmx)}, identical prefix {n_same}")
+    p = O.Problem.from_case(case)
+    ev = O.evaluate(p, mix.design())
+    o, _ = mix.eval_ports()
+    err = s_rel(case, o, ev.o)
+    print(f"mixed final-design S error vs oracle {err:.2e}")
+    assert err < 1e-4
+    assert n_same >= min(100, len(k64))
