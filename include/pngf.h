@@ -137,6 +137,32 @@ pngf_status pngf_score_flips(pngf_ctx* ctx, const int32_t* pixels, int32_t n, do
 pngf_status pngf_accept_flip(pngf_ctx* ctx, int32_t pixel);
 
 /*
+ * pngf_accept_flip for callers that cannot allocate device memory: the same
+ * kept-flip update, but its scratch (the pivot record and the gathered
+ * column of W) lives in a fixed array inside the library instead of the
+ * workspace.  It exists for callers that may not allocate device memory
+ * while they run: code whose device memory was reserved up front by another
+ * component (a framework's caching allocator that owns the whole pool), or a
+ * latency-bound loop that must not block on the device-wide synchronisation a
+ * cudaMalloc or cudaFree can imply.  Such callers set up the context and its
+ * workspace once, beforehand, and then only pass it in.  The paper has no
+ * counterpart to this entry point.
+ *
+ *   - FP64 contexts only, and n_d <= PNGF_NOALLOC_MAX_ND (8192), else
+ *     PNGF_EINVAL; the context's device must be the current device.
+ *   - The array (256 + 16 * PNGF_NOALLOC_MAX_ND bytes, about 128 KiB) is held
+ *     by every GPU that loads the library, until the process exits.
+ *   - The first call on a device looks the array's device address up once
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call and every context share the one array: calls that overlap on
+ *     the GPU (other streams, other contexts) race with each other; order them
+ *     on one stream.  Each call overwrites the array before it reads it.
+ *   - It allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ */
+#define PNGF_NOALLOC_MAX_ND 8192
+pngf_status pngf_accept_flip_noalloc(pngf_ctx* ctx, int32_t pixel);
+
+/*
  * Run direct binary search on the device: up to n_sweeps passes over the
  * pixels; a pass that keeps no flip ends the search (converged).
  *   order     int32 n_sweeps x n_d (device): visiting order of each pass, each

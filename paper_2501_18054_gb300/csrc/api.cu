@@ -166,6 +166,14 @@ pngf_status pngf_accept_flip(pngf_ctx* c, int32_t pixel) {
   return c->cfg.precision == PNGF_MIXED ? accept_flip_mixed(c, pixel) : accept_flip(c, pixel);
 }
 
+pngf_status pngf_accept_flip_noalloc(pngf_ctx* c, int32_t pixel) {
+  if (!c || pixel < 0 || pixel >= c->cfg.n_d) return PNGF_EINVAL;
+  if (c->cfg.precision != PNGF_FP64) return PNGF_EINVAL;
+  if (c->cfg.n_d > PNGF_NOALLOC_MAX_ND) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  return accept_flip_noalloc(c, pixel);
+}
+
 pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, int32_t* trace,
                            double* trace_f, int32_t trace_cap, int64_t* counters) {
   if (!c || n_sweeps < 0 || trace_cap < 0) return PNGF_EINVAL;

@@ -163,6 +163,7 @@ pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* 
                       double* trace_f, int32_t trace_cap, int64_t* counters);
 pngf_status score_flips(pngf_ctx* c, const int32_t* pixels, int n, double* f_new, double* o_new);
 pngf_status accept_flip(pngf_ctx* c, int pixel);
+pngf_status accept_flip_noalloc(pngf_ctx* c, int pixel);
 int sweep_grid_size(pngf_ctx* c);
 
 inline pngf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PNGF_OK : PNGF_ECUDA; }

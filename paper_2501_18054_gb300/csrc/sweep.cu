@@ -20,6 +20,7 @@
 // plus generation word with a bounded spin: a barrier that waits longer than
 // the spin limit latches PNGF_ETIMEOUT and every CTA returns.
 #include <cstdio>
+#include <mutex>
 
 #include "sweep_common.cuh"
 
@@ -380,6 +381,50 @@ pngf_status score_flips(pngf_ctx* c, const int32_t* pixels, int m, double* f_new
 pngf_status accept_flip(pngf_ctx* c, int pixel) {
   SweepArgs a = make_args(c);
   PivotRecord* rec = reinterpret_cast<PivotRecord*>(a.rbuf);  // scratch
+  accept_pivot_kernel<<<1, 32, 0, c->stream>>>(a, pixel, rec);
+  accept_gather_kernel<<<c->n_sm, 256, 0, c->stream>>>(a, pixel);
+  accept_update_kernel<<<c->n_sm * 2, kThreads, 0, c->stream>>>(a, rec);
+  return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- accept without workspace scratch
+// Scratch of the kept-flip update (the pivot record and the gathered column c)
+// in a fixed device array instead of the caller's workspace, for callers that
+// must not allocate device memory at all.  Every GPU that loads the library
+// holds this array until the process exits.
+constexpr int kNoAllocRecordBytes = 256;
+static_assert(sizeof(PivotRecord) <= kNoAllocRecordBytes, "pivot record slot");
+static __device__ __align__(256) unsigned char g_accept_scratch[kNoAllocRecordBytes +
+                                                               PNGF_NOALLOC_MAX_ND * sizeof(c128)];
+
+constexpr int kMaxDevices = 64;
+static void* g_accept_scratch_ptr[kMaxDevices];
+static std::mutex g_accept_scratch_mu;
+
+// Device address of the array on the current device; resolved once per device.
+static pngf_status accept_scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return PNGF_EINVAL;
+  std::lock_guard<std::mutex> lock(g_accept_scratch_mu);
+  if (!g_accept_scratch_ptr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_accept_scratch) != cudaSuccess || !p) return PNGF_ECUDA;
+    g_accept_scratch_ptr[device] = p;
+  }
+  *out = g_accept_scratch_ptr[device];
+  return PNGF_OK;
+}
+
+pngf_status accept_flip_noalloc(pngf_ctx* c, int pixel) {
+  if (c->cfg.n_d > PNGF_NOALLOC_MAX_ND) return PNGF_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PNGF_ECUDA;
+  if (dev != c->device) return PNGF_EINVAL;
+  void* base = nullptr;
+  pngf_status st = accept_scratch_address(dev, &base);
+  if (st != PNGF_OK) return st;
+  SweepArgs a = make_args(c);
+  PivotRecord* rec = static_cast<PivotRecord*>(base);
+  a.cbuf = reinterpret_cast<c128*>(static_cast<unsigned char*>(base) + kNoAllocRecordBytes);
   accept_pivot_kernel<<<1, 32, 0, c->stream>>>(a, pixel, rec);
   accept_gather_kernel<<<c->n_sm, 256, 0, c->stream>>>(a, pixel);
   accept_update_kernel<<<c->n_sm * 2, kThreads, 0, c->stream>>>(a, rec);

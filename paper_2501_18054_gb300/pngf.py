@@ -25,6 +25,7 @@ PNGF_FP64, PNGF_MIXED = 0, 1
 PNGF_FIRST_IMPROVEMENT, PNGF_BEST_IMPROVEMENT = 0, 1
 PNGF_OBJ_MAX_WEIGHTED_POWER, PNGF_OBJ_MIN_INSERTION_LOSS = 0, 1
 PNGF_MAX_PORTS = 8
+PNGF_NOALLOC_MAX_ND = 8192
 
 
 class pngf_config(ctypes.Structure):
@@ -70,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "pngf_factor": (st, [_P, _P]),
             "pngf_score_flips": (st, [_P, _P, ctypes.c_int32, _P, _P]),
             "pngf_accept_flip": (st, [_P, ctypes.c_int32]),
+            "pngf_accept_flip_noalloc": (st, [_P, ctypes.c_int32]),
             "pngf_dbs_sweep": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]),
             "pngf_eval_ports": (st, [_P, _P, _P]),
             "pngf_get_design": (st, [_P, _P]),
@@ -94,6 +96,7 @@ def exported_symbols() -> list:
     L = lib()
     names = []
     for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
+              "pngf_accept_flip_noalloc",
               "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state", "pngf_snapshot",
               "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
         if hasattr(L, n):
@@ -135,6 +138,10 @@ def pngf_score_flips(ctx: int, pixels: int, n: int, f_new: int, o_new: Optional[
 
 def pngf_accept_flip(ctx: int, pixel: int) -> None:
     _check(lib().pngf_accept_flip(ctx, int(pixel)), "pngf_accept_flip")
+
+
+def pngf_accept_flip_noalloc(ctx: int, pixel: int) -> None:
+    _check(lib().pngf_accept_flip_noalloc(ctx, int(pixel)), "pngf_accept_flip_noalloc")
 
 
 def pngf_dbs_sweep(ctx: int, n_sweeps: int, order: Optional[int], trace: Optional[int],
