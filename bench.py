@@ -281,8 +281,9 @@ def main():
         assert int(c2[1]) == evals_per_step, "steps are not identical runs"
         cyc = ctx.phase_cycles()
         mhz = clk.get("sm_mhz") or 2070.0
-        phase_names = ["score", "wait_after_score", "select_pivot_gather", "wait_before_update",
-                       "update_rank1", "refresh", "sweep_setup", "kernel_total"]
+        phase_names = ["score", "wait_after_score", "select_pivot_gather", "wait_or_flush",
+                       "update", "refresh", "sweep_setup", "kernel_total", "refresh_x", "refresh_residual",
+                       "refresh_correct", "refresh_ports"]
         phase_ms = {nm: float(cv) / (mhz * 1e3) for nm, cv in zip(phase_names, cyc)}
         ms = t0.elapsed_time(t1)
         ms_max = dist.max(torch, ms, dev)

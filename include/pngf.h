@@ -205,12 +205,14 @@ pngf_status pngf_restore(pngf_ctx* ctx);
 
 /*
  * Tracing: SM clock cycles that CTA 0 of the last pngf_dbs_sweep spent per
- * phase, host int64 x 8: [0] scoring, [1] wait after scoring, [2] selection,
- * pivot and column gather, [3] wait before the update, [4] state update and
- * rank-1 update of W, [5] FP64 refreshes, [6] sweep set-up, [7] whole kernel.
+ * phase, host int64 x 16: [0] scoring, [1] wait after scoring, [2] selection,
+ * pivot and column gather, [3] wait before the update (FP64) / flush of the
+ * delayed set (mixed), [4] state update (and the rank-1 update of W on the
+ * FP64 path), [5] FP64 refreshes, [6] sweep set-up, [7] whole kernel,
+ * [8..11] refresh sub-phases (x, residual, correction, ports), [12..15] 0.
  * Synchronizes the stream.
  */
-pngf_status pngf_get_phase_cycles(pngf_ctx* ctx, int64_t* host8);
+pngf_status pngf_get_phase_cycles(pngf_ctx* ctx, int64_t* host16);
 
 /* Synchronize the stream and return the latched device status (then clear it). */
 pngf_status pngf_sync(pngf_ctx* ctx);

@@ -34,7 +34,7 @@ Layout make_layout(const pngf_config& cfg) {
   const size_t plane = n * L.ldl * sizeof(float);
   L.Wlo_re = take(mixed ? 2 * plane : 0);
   L.Wlo_im = L.Wlo_re + (mixed ? plane : 0);
-  L.X = take(n * (size_t)L.R * c);
+  L.X = take(n * (size_t)L.R * 2 * sizeof(float));
   L.xa = take((size_t)L.R * c);
   L.snapW_bytes = mixed ? off - L.Wlo_re : n * L.ldw * c;
   // contiguous state block: diag, e, T, v, b
@@ -267,10 +267,10 @@ pngf_status pngf_restore(pngf_ctx* c) {
   return PNGF_OK;
 }
 
-pngf_status pngf_get_phase_cycles(pngf_ctx* c, int64_t* host8) {
-  if (!c || !host8) return PNGF_EINVAL;
+pngf_status pngf_get_phase_cycles(pngf_ctx* c, int64_t* host16) {
+  if (!c || !host16) return PNGF_EINVAL;
   Control* ctl = at<Control>(c, c->L.ctl);
-  if (cudaMemcpyAsync(host8, ctl->phase_cycles, 8 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream) !=
+  if (cudaMemcpyAsync(host16, ctl->phase_cycles, 16 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return PNGF_ECUDA;

@@ -100,7 +100,8 @@ struct Control {
   unsigned int bar_count;   // grid barrier arrivals
   unsigned int bar_gen;     // grid barrier generation
   long long counters[8];    // see pngf_dbs_sweep
-  long long phase_cycles[8];  // SM cycles of CTA 0 per sweep phase (last sweep)
+  unsigned long long sel[3];  // FIRST mode: per-round minimum of (position << 10 | cta), 3 rotating cells
+  long long phase_cycles[16];  // SM cycles of CTA 0 per sweep phase (last sweep)
   double f;                 // current objective
   int factored;
   int n_acc_total;          // accepted flips since the last factor / restore

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
   int sweeps_done = 0, converged = 0, status = PNGF_OK;
   // per-phase SM-cycle accounting of CTA 0 (thread 0 sees every phase boundary)
   const bool timer = (cta == 0 && threadIdx.x == 0);
-  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long ph[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   long long t_last = clock64(), t_begin = t_last;
   auto tick = [&](int phase) {
     if (timer) {
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     }
   };
   int since_refresh = ctl->since_refresh;
-  int s = 0, t = 0, acc_in_sweep = 0, slot = 0;
+  int s = 0, t = 0, acc_in_sweep = 0, slot = 0, rd = 0;
   bool failed = false;
 
   // inverse permutation of the sweep's visiting order; an entry outside
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
         if (gain_of(s_op, fn, f) - thr > 0.0 && pos < best) best = pos;
       }
       best = block_min_ll(best);
-      if (threadIdx.x == 0) a.part_key[slot * P + cta] = best;
+      if (threadIdx.x == 0) sel_offer(ctl, rd, best, cta);
       tick(0);
     } else {
       double g = -INFINITY;
@@ -120,11 +120,9 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       const int lane = threadIdx.x;
       int k = -1, pos_k = -1;
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-        long long best = LLONG_MAX;
-        for (int q = lane; q < P; q += 32) best = min(best, a.part_key[slot * P + q]);
-        for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-        if (best != LLONG_MAX) {
-          pos_k = (int)best;
+        unsigned long long key = sel_read(ctl, rd);
+        if (key != ~0ull) {
+          pos_k = (int)(key >> 10);
           k = a.order ? a.order[(size_t)s * n + pos_k] : pos_k;
           if ((unsigned)k >= (unsigned)n) k = -2;  // invalid order entry
         }
@@ -157,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     }
     __syncthreads();
     slot ^= 1;
+    ++rd;
     const int k = s_k, pos_k = s_pos;
     if (k == -2 || *reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) {
       status = PNGF_EINVAL;
@@ -223,14 +222,19 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       since_refresh = 0;
       ++n_refresh;
       if (!grid_sync(ctl)) { failed = true; break; }
+      tick(5);
       refresh_x(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
+      tick(8);
       refresh_residual(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
+      tick(9);
       refresh_correct(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
+      tick(10);
       ports_partial(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
+      tick(11);
       if (threadIdx.x == 0) {
         FOR_PORTS(p, a.n_o) {
           c128 acc = mk(0.0, 0.0);
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     ctl->counters[6] = status;
     ctl->counters[7] = 0;
     ph[7] = clock64() - t_begin;
-    for (int q = 0; q < 8; ++q) ctl->phase_cycles[q] = ph[q];
+    for (int q = 0; q < 16; ++q) ctl->phase_cycles[q] = ph[q];
     if (a.counters)
       for (int q = 0; q < 8; ++q) a.counters[q] = ctl->counters[q];
     if (status == PNGF_ENUMERIC || status == PNGF_ETIMEOUT || status == PNGF_EINVAL) latch_status(ctl, status);
@@ -361,6 +365,8 @@ pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* 
   Control* ctl = a.ctl;
   // reset the barrier words (a previous launch that timed out may have left them set)
   cudaError_t err = cudaMemsetAsync(&ctl->bar_count, 0, 2 * sizeof(unsigned), c->stream);
+  if (err != cudaSuccess) return PNGF_ECUDA;
+  err = cudaMemsetAsync(&ctl->sel[0], 0xff, sizeof(ctl->sel), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
   int grid = c->coop_ctas;
   void* params[] = {&a};

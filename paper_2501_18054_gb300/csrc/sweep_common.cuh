@@ -41,7 +41,7 @@ struct SweepArgs {
   int mixed, ldl, R;
   float* Wr;  // planar FP32 copy of W (upper triangle current)
   float* Wi;
-  c128* X;    // n x R delayed columns c_i (row j holds c_0[j] .. c_{R-1}[j])
+  float2* X;  // n x R delayed columns c_i in FP32 (row j holds c_0[j] .. c_{R-1}[j])
   c128* xa;   // R coefficients alpha_i
   void* rec;  // [2][P] candidate records
 };
@@ -52,7 +52,8 @@ struct CandRecord {
   double gain;
   int pixel;
   int b;
-  c128 diag, e, dv;
+  c128 alpha, coef;  // Sherman-Morrison coefficient of the flip and alpha * e_k
+  c128 dv;
   c128 T[kMaxPorts];
 };
 
@@ -90,6 +91,21 @@ __device__ bool grid_sync(Control* ctl) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- FIRST-mode selection cells
+// Round rd of the search uses cell sel[rd % 3]: every CTA with a candidate
+// atomically lowers it to (position << 10 | cta) before the round's barrier,
+// and every CTA reads it after.  CTA 0 re-arms the cell of round rd + 1 during
+// round rd: its last readers (round rd - 2) finished before barrier rd - 1,
+// and its first writers (round rd + 1) start after barrier rd.
+__device__ __forceinline__ void sel_offer(Control* ctl, int rd, long long pos, int cta) {
+  if (pos != LLONG_MAX) atomicMin(&ctl->sel[rd % 3], ((unsigned long long)pos << 10) | (unsigned)cta);
+  if (cta == 0) ctl->sel[(rd + 1) % 3] = ~0ull;
+}
+
+__device__ __forceinline__ unsigned long long sel_read(Control* ctl, int rd) {
+  return *reinterpret_cast<volatile unsigned long long*>(&ctl->sel[rd % 3]);
 }
 
 // ---------------------------------------------------------------- block reductions
@@ -145,7 +161,8 @@ __device__ void block_best(double& g, int& p) {
 // Candidate objective for flipping pixel j against the current state (Eq. 14).
 // Returns false for a numerically singular candidate (|d_j| < 1e-14).
 __device__ __forceinline__ bool score_pixel(const SweepArgs& a, const ObjParams& op, int j, const c128* o,
-                                            double& f_new, c128* o_new) {
+                                            double& f_new, c128* o_new, c128* alpha_out = nullptr,
+                                            c128* coef_out = nullptr) {
   c128 dvj = a.dv[j];
   c128 delta = a.b[j] ? mk(-dvj.x, -dvj.y) : dvj;
   c128 dj = csub(mk(1.0, 0.0), cmul(delta, a.diag[j]));
@@ -160,6 +177,10 @@ __device__ __forceinline__ bool score_pixel(const SweepArgs& a, const ObjParams&
     fn += objective_term(op, p, on);
   }
   f_new = fn;
+  if (alpha_out) {
+    *alpha_out = alpha;
+    *coef_out = coef;
+  }
   return true;
 }
 
@@ -281,6 +302,11 @@ __device__ __forceinline__ c128* rvec(const SweepArgs& a, int blk, int q) {
   return a.rbuf + ((size_t)blk * (1 + a.n_o) + q) * a.n;
 }
 
+// block 2 holds x2 = v.r in FP32 (it only feeds the FP32 correction product)
+__device__ __forceinline__ float2* x2f(const SweepArgs& a, int q) {
+  return reinterpret_cast<float2*>(rvec(a, 2, 0)) + (size_t)q * a.n;
+}
+
 __device__ __forceinline__ c128 warp_sum(c128 v) {
   for (int off = 16; off > 0; off >>= 1) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
@@ -298,28 +324,35 @@ __device__ void refresh_x(const SweepArgs& a, int pb, int pe) {
   }
 }
 
+// The refresh kernels carry the number of refined vectors NV = 1 + n_o as a
+// template parameter: every loop over the vectors is then fully unrolled with
+// no predicated-off FP64 work (the FP64 pipe is the scarce one on GB300).
+
 // R1: residuals of own rows (row j of G dotted with x), and x2 = v.r
-#define FOR_VECS(q, nv) _Pragma("unroll") for (int q = 0; q < 1 + kMaxPorts; ++q) if (q < (nv))
-__device__ __noinline__ void refresh_residual(const SweepArgs& a, int pb, int pe) {
+template <int NV>
+__device__ __noinline__ void refresh_residual_t(const SweepArgs& a, int pb, int pe) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nv = 1 + a.n_o;
   for (int j = pb + warp; j < pe; j += nw) {
     const c128* g = a.G + (size_t)j * a.n;
-    c128 acc[1 + kMaxPorts];
-    FOR_VECS(q, nv) acc[q] = mk(0.0, 0.0);
+    c128 acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = mk(0.0, 0.0);
 #pragma unroll 4
     for (int i = lane; i < a.n; i += 32) {
       c128 gi = g[i];
-      FOR_VECS(q, nv) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
     }
-    FOR_VECS(q, nv) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
       c128 sum = warp_sum(acc[q]);
       if (lane == 0) {
         c128 rhs = q == 0 ? a.cd[j] : a.God[(size_t)(q - 1) * a.n + j];
         c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
         c128 r = cadd(csub(rhs, y), sum);
         rvec(a, 0, q)[j] = r;
-        rvec(a, 2, q)[j] = cmul(a.v[j], r);
+        c128 x2 = cmul(a.v[j], r);
+        x2f(a, q)[j] = make_float2((float)x2.x, (float)x2.y);
       }
     }
   }
@@ -356,20 +389,26 @@ __device__ __forceinline__ f2c w_upper(const SweepArgs& a, int i, int j) {
   return f2(a.W[(size_t)i * a.ldw + j]);
 }
 
-__device__ __noinline__ void refresh_correct(const SweepArgs& a, int pb, int pe) {
+template <int NV>
+__device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int pe) {
   __shared__ f2c red[kThreads / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nv = 1 + a.n_o;
   // upper part, one warp per own row
   for (int j = pb + warp; j < pe; j += nw) {
-    f2c acc[1 + kMaxPorts];
-    FOR_VECS(q, nv) acc[q] = f2c{0.f, 0.f};
+    f2c acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
 #pragma unroll 4
     for (int i = j + lane; i < a.n; i += 32) {
       f2c wi = w_upper(a, j, i);
-      FOR_VECS(q, nv) acc[q] = f2fma(wi, f2(rvec(a, 2, q)[i]), acc[q]);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        float2 x = x2f(a, q)[i];
+        acc[q] = f2fma(wi, f2c{x.x, x.y}, acc[q]);
+      }
     }
-    FOR_VECS(q, nv) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
       f2c sum = f2sum(acc[q]);
       if (lane == 0) rvec(a, 3, q)[j] = mk(sum.x, sum.y);
     }
@@ -379,19 +418,23 @@ __device__ __noinline__ void refresh_correct(const SweepArgs& a, int pb, int pe)
   for (int c0 = pb; c0 < pe; c0 += 32) {
     const int j = c0 + lane;
     const int rows = min(pe, c0 + 32) - 1;  // rows i < j <= rows
-    f2c acc[1 + kMaxPorts];
-    FOR_VECS(q, nv) acc[q] = f2c{0.f, 0.f};
+    f2c acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
 #pragma unroll 4
     for (int i = warp; i < rows; i += nw) {
       if (i < j && j < pe) {
         f2c wij = w_upper(a, i, j);
-        FOR_VECS(q, nv) acc[q] = f2fma(wij, f2(rvec(a, 2, q)[i]), acc[q]);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          float2 x = x2f(a, q)[i];
+          acc[q] = f2fma(wij, f2c{x.x, x.y}, acc[q]);
+        }
       }
     }
-    for (int q = 0; q < nv; ++q) {
-      f2c mine = f2c{0.f, 0.f};
-      FOR_VECS(qq, nv) if (qq == q) mine = acc[qq];
-      red[warp][lane] = mine;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      red[warp][lane] = acc[q];
       __syncthreads();
       if (warp == 0 && j < pe) {
         double lx = 0.0, ly = 0.0;
@@ -412,25 +455,45 @@ __device__ __noinline__ void refresh_correct(const SweepArgs& a, int pb, int pe)
   }
 }
 
+__device__ void refresh_residual(const SweepArgs& a, int pb, int pe) {
+  switch (a.n_o) {
+    case 1: refresh_residual_t<2>(a, pb, pe); break;
+    case 2: refresh_residual_t<3>(a, pb, pe); break;
+    case 3: refresh_residual_t<4>(a, pb, pe); break;
+    case 4: refresh_residual_t<5>(a, pb, pe); break;
+    case 5: refresh_residual_t<6>(a, pb, pe); break;
+    case 6: refresh_residual_t<7>(a, pb, pe); break;
+    case 7: refresh_residual_t<8>(a, pb, pe); break;
+    default: refresh_residual_t<9>(a, pb, pe); break;
+  }
+}
+
+__device__ void refresh_correct(const SweepArgs& a, int pb, int pe) {
+  switch (a.n_o) {
+    case 1: refresh_correct_t<2>(a, pb, pe); break;
+    case 2: refresh_correct_t<3>(a, pb, pe); break;
+    case 3: refresh_correct_t<4>(a, pb, pe); break;
+    case 4: refresh_correct_t<5>(a, pb, pe); break;
+    case 5: refresh_correct_t<6>(a, pb, pe); break;
+    case 6: refresh_correct_t<7>(a, pb, pe); break;
+    case 7: refresh_correct_t<8>(a, pb, pe); break;
+    default: refresh_correct_t<9>(a, pb, pe); break;
+  }
+}
+
 // partial o sums of pixels [pb, pe) -> opart[cta]
 __device__ __noinline__ void ports_partial(const SweepArgs& a, int pb, int pe) {
   __shared__ c128 red[kMaxPorts][kThreads / 32];
-  c128 acc[kMaxPorts];
-  FOR_PORTS(p, a.n_o) acc[p] = mk(0.0, 0.0);
-  for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
-    c128 ve = cmul(a.v[j], a.e[j]);
-    FOR_PORTS(p, a.n_o) acc[p] = cfma(a.God[(size_t)p * a.n + j], ve, acc[p]);
-  }
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  FOR_PORTS(p, a.n_o) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int p = 0; p < a.n_o; ++p) {
+    c128 acc = mk(0.0, 0.0);
+    for (int j = pb + threadIdx.x; j < pe; j += blockDim.x)
+      acc = cfma(a.God[(size_t)p * a.n + j], cmul(a.v[j], a.e[j]), acc);
     for (int off = 16; off > 0; off >>= 1) {
-      acc[p].x += __shfl_down_sync(0xffffffffu, acc[p].x, off);
-      acc[p].y += __shfl_down_sync(0xffffffffu, acc[p].y, off);
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
     }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    FOR_PORTS(p, a.n_o) red[p][w] = acc[p];
+    if (lane == 0) red[p][w] = acc;
   }
   __syncthreads();
   if (threadIdx.x < a.n_o) {
@@ -473,7 +536,7 @@ SweepArgs make_args(pngf_ctx* c) {
   a.R = L.R;
   a.Wr = at<float>(c, L.Wlo_re);
   a.Wi = at<float>(c, L.Wlo_im);
-  a.X = at<c128>(c, L.X);
+  a.X = at<float2>(c, L.X);
   a.xa = at<c128>(c, L.xa);
   a.rec = c->ws + L.rec;
   return a;

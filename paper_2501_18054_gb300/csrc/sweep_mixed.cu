@@ -6,8 +6,10 @@
 // Everything that decides a flip stays FP64: diag(W), e, T, o, the
 // Sherman-Morrison denominators d_k and alpha (Eqs. 9 and 14).  Per kept flip
 // of pixel k only the column c = W[:,k] is needed:
-//   c_j = W_lo(k, j) + sum_{i<r} (alpha_i x_i[k]) x_i[j]      (FP32 base + FP64 sum)
+//   c_j = W_lo(k, j) + sum_{i<r} (alpha_i x_i[k]) x_i[j]      (FP32 arithmetic)
 // which updates diag(W), e and T in FP64 and is appended to the delayed set.
+// On GB300 the FP64 pipe retires 2 DFMA per clock per SM (1/64 of FP32), so
+// everything that only has to be FP32-accurate runs on the FP32 pipe.
 // Every R kept flips the delayed set is folded into W_lo with one rank-R
 // product over the upper triangle (the paper's O(N_opt^2) update of
 // Supplementary Note 3, done once per R flips), and every refresh_k flips e
@@ -31,23 +33,30 @@ __device__ __forceinline__ CandRecord* rec_at(const SweepArgs& a, int slot, int 
 }
 
 __device__ __forceinline__ void fill_record(const SweepArgs& a, CandRecord* r, int j, long long key,
-                                            double gain) {
+                                            double gain, c128 alpha, c128 coef) {
   r->key = key;
   r->gain = gain;
   r->pixel = j;
   r->b = a.b[j];
-  r->diag = a.diag[j];
-  r->e = a.e[j];
+  r->alpha = alpha;
+  r->coef = coef;
   r->dv = a.dv[j];
   for (int p = 0; p < a.n_o; ++p) r->T[p] = a.T[(size_t)p * a.ldt + j];
 }
 
+// record of pixel j built from the state alone (single-call accept path)
+__device__ __forceinline__ void fill_record_from_state(const SweepArgs& a, CandRecord* r, int j) {
+  c128 dvj = a.dv[j];
+  c128 delta = a.b[j] ? mk(-dvj.x, -dvj.y) : dvj;
+  c128 dj = csub(mk(1.0, 0.0), cmul(delta, a.diag[j]));
+  c128 alpha = cdiv(delta, dj);
+  fill_record(a, r, j, 0, 0.0, alpha, cmul(alpha, a.e[j]));
+}
+
 __device__ __forceinline__ void pivot_from_record(const CandRecord& r, int n_o, Pivot& pv) {
-  c128 delta = r.b ? mk(-r.dv.x, -r.dv.y) : r.dv;
-  c128 dk = csub(mk(1.0, 0.0), cmul(delta, r.diag));
   pv.k = r.pixel;
-  pv.alpha = cdiv(delta, dk);
-  pv.coef = cmul(pv.alpha, r.e);
+  pv.alpha = r.alpha;
+  pv.coef = r.coef;
   for (int p = 0; p < n_o; ++p) pv.Tk[p] = r.T[p];
 }
 
@@ -60,25 +69,45 @@ __device__ __forceinline__ c128 wlo_sym(const SweepArgs& a, int i, int j) {
 
 // column assembly + state update for own pixels; appends c to the delayed set.
 // One warp per pixel: lanes split the delayed sum, a shuffle reduction adds it.
-__device__ void mixed_accept_own(const SweepArgs& a, const Pivot& pv, const c128* beta, int r, int pb, int pe) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = pb + warp; j < pe; j += nw) {
-    const c128* xj = a.X + (size_t)j * a.R;
-    c128 part = mk(0.0, 0.0);
-    for (int i = lane; i < r; i += 32) part = cfma(beta[i], xj[i], part);
-    for (int off = 16; off > 0; off >>= 1) {
-      part.x += __shfl_xor_sync(0xffffffffu, part.x, off);
-      part.y += __shfl_xor_sync(0xffffffffu, part.y, off);
+__device__ void mixed_accept_own(const SweepArgs& a, const Pivot& pv, const float2* beta, int r, int pb, int pe) {
+  constexpr int kChunk = 256;
+  __shared__ c128 s_w[kChunk];
+  __shared__ float2 s_sum[kChunk];
+  const int g = threadIdx.x >> 4, gl = threadIdx.x & 15, ng = blockDim.x >> 4;
+  const unsigned half = 0xffffu << (threadIdx.x & 16);
+  for (int base = pb; base < pe; base += kChunk) {
+    const int cnt = min(kChunk, pe - base);
+    // U1: one thread per pixel fetches W_lo(k, j) (row k or column k)
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) s_w[t] = wlo_sym(a, pv.k, base + t);
+    // U2: a 16-lane group per pixel forms the delayed sum in FP32
+    for (int t = g; t < cnt; t += ng) {
+      const float2* xj = a.X + (size_t)(base + t) * a.R;
+      float px = 0.f, py = 0.f;
+      for (int i = gl; i < r; i += 16) {
+        float2 b = beta[i], x = xj[i];
+        px = fmaf(b.x, x.x, fmaf(-b.y, x.y, px));
+        py = fmaf(b.x, x.y, fmaf(b.y, x.x, py));
+      }
+      for (int off = 8; off > 0; off >>= 1) {
+        px += __shfl_xor_sync(half, px, off);
+        py += __shfl_xor_sync(half, py, off);
+      }
+      if (gl == 0) s_sum[t] = make_float2(px, py);
     }
-    if (lane == 0) {
-      c128 cj = cadd(wlo_sym(a, pv.k, j), part);
-      a.X[(size_t)j * a.R + r] = cj;
+    __syncthreads();
+    // U3: one thread per pixel appends c_j and updates diag(W), e, T in FP64
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int j = base + t;
+      c128 dj = a.diag[j], ej = a.e[j];
+      c128 cj = mk(s_w[t].x + (double)s_sum[t].x, s_w[t].y + (double)s_sum[t].y);
       c128 aj = cmul(pv.alpha, cj);
-      a.diag[j] = cfma(aj, cj, a.diag[j]);
-      a.e[j] = cfma(pv.coef, cj, a.e[j]);
+      a.X[(size_t)j * a.R + r] = make_float2((float)cj.x, (float)cj.y);
+      a.diag[j] = cfma(aj, cj, dj);
+      a.e[j] = cfma(pv.coef, cj, ej);
+#pragma unroll 1
       for (int p = 0; p < a.n_o; ++p) {
-        c128* t = a.T + (size_t)p * a.ldt + j;
-        *t = cfma(aj, pv.Tk[p], *t);
+        c128* tp = a.T + (size_t)p * a.ldt + j;
+        *tp = cfma(aj, pv.Tk[p], *tp);
       }
       if (j == pv.k) {
         uint8_t nb = a.b[j] ^ 1;
@@ -86,6 +115,17 @@ __device__ void mixed_accept_own(const SweepArgs& a, const Pivot& pv, const c128
         a.v[j] = nb ? a.dv[j] : mk(0.0, 0.0);
       }
     }
+    __syncthreads();
+  }
+}
+
+// beta_i = alpha_i x_i[k] in FP32 for the delayed columns
+__device__ __forceinline__ void make_beta(const SweepArgs& a, int k, int r, float2* beta) {
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    c128 al = a.xa[i];
+    float2 x = a.X[(size_t)k * a.R + i];
+    float ax = (float)al.x, ay = (float)al.y;
+    beta[i] = make_float2(fmaf(ax, x.x, -ay * x.y), fmaf(ax, x.y, ay * x.x));
   }
 }
 
@@ -103,23 +143,30 @@ __device__ void flush_tiles(const SweepArgs& a, int r, float* smem) {
   const int n = a.n;
   const int tn = (n + FT - 1) / FT;
   const long long n_tiles = (long long)tn * (tn + 1) / 2;
-  f2x* Ys = reinterpret_cast<f2x*>(smem);          // [r][FT]   rows of tile I, times alpha
-  f2x* Xs = Ys + FT * kMaxDelay;                     // [r][FT]   rows of tile J
+  constexpr int LD = FT + 1;                         // padded rows: no bank conflicts on the fills
+  f2x* Ys = reinterpret_cast<f2x*>(smem);          // [r][LD]   rows of tile I, times alpha
+  f2x* Xs = Ys + LD * kMaxDelay;                     // [r][LD]   rows of tile J
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 32 threads
+  __shared__ float2 s_alpha[kMaxDelay];
+  __syncthreads();
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    c128 al = a.xa[q];
+    s_alpha[q] = make_float2((float)al.x, (float)al.y);
+  }
   for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     int I, J;
     tri_rc(t, tn, I, J);
     const int i0 = I * FT, j0 = J * FT;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < FT * r; idx += blockDim.x) {
-      int rr = idx / r, q = idx % r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int rr = warp; rr < FT; rr += nw)
+    for (int q = lane; q < r; q += 32) {
       int gi = i0 + rr, gj = j0 + rr;
-      c128 al = a.xa[q];
-      c128 xi = gi < n ? a.X[(size_t)gi * a.R + q] : mk(0.0, 0.0);
-      c128 xj = gj < n ? a.X[(size_t)gj * a.R + q] : mk(0.0, 0.0);
-      c128 yi = cmul(al, xi);
-      Ys[q * FT + rr] = f2x{(float)yi.x, (float)yi.y};
-      Xs[q * FT + rr] = f2x{(float)xj.x, (float)xj.y};
+      float2 al = s_alpha[q];
+      float2 xi = gi < n ? a.X[(size_t)gi * a.R + q] : make_float2(0.f, 0.f);
+      float2 xj = gj < n ? a.X[(size_t)gj * a.R + q] : make_float2(0.f, 0.f);
+      Ys[q * LD + rr] = f2x{fmaf(al.x, xi.x, -al.y * xi.y), fmaf(al.x, xi.y, al.y * xi.x)};
+      Xs[q * LD + rr] = f2x{xj.x, xj.y};
     }
     __syncthreads();
     // thread (ty, tx) owns rows ty, ty+32 and columns tx, tx+16, tx+32, tx+48
@@ -131,9 +178,9 @@ __device__ void flush_tiles(const SweepArgs& a, int r, float* smem) {
     for (int q = 0; q < r; ++q) {
       f2x y[2], x[4];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) y[u] = Ys[q * FT + ty + 32 * u];
+      for (int u = 0; u < 2; ++u) y[u] = Ys[q * LD + ty + 32 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = Xs[q * FT + tx + 16 * v];
+      for (int v = 0; v < 4; ++v) x[v] = Xs[q * LD + tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -170,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ Pivot s_pv;
   __shared__ int s_k, s_pos;
   __shared__ ObjParams s_op;
-  __shared__ c128 s_beta[kMaxDelay];
+  __shared__ float2 s_beta[kMaxDelay];
   if (threadIdx.x == 0) {
     s_op = a.op;
     FOR_PORTS(p, a.n_o) s_o[p] = ctl->o[p];
@@ -181,10 +228,10 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   int sweeps_done = 0, converged = 0, status = PNGF_OK;
   int since_refresh = ctl->since_refresh;
   int r = ctl->r_delay;
-  int s = 0, t = 0, acc_in_sweep = 0, slot = 0;
+  int s = 0, t = 0, acc_in_sweep = 0, slot = 0, rd = 0;
   bool failed = false;
   const bool timer = (cta == 0 && threadIdx.x == 0);
-  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long ph[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   long long t_last = clock64(), t_begin = t_last;
   auto tick = [&](int phase) {
     if (timer) {
@@ -222,27 +269,39 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       long long best = LLONG_MAX;
       double g = -INFINITY;
       int pix = INT_MAX;
+      c128 b_alpha = mk(0.0, 0.0), b_coef = b_alpha;
       for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
         double fn;
+        c128 al, co;
         if (a.mode == PNGF_FIRST_IMPROVEMENT) {
           int pos = a.order ? a.pos_of[j] : j;
           if (pos < t) continue;
-          if (!score_pixel(a, s_op, j, s_o, fn, nullptr)) continue;
-          if (gain_of(s_op, fn, f) - thr > 0.0 && pos < best) { best = pos; pix = j; }
+          if (!score_pixel(a, s_op, j, s_o, fn, nullptr, &al, &co)) continue;
+          if (gain_of(s_op, fn, f) - thr > 0.0 && pos < best) {
+            best = pos;
+            pix = j;
+            b_alpha = al;
+            b_coef = co;
+          }
         } else {
-          if (!score_pixel(a, s_op, j, s_o, fn, nullptr)) continue;
+          if (!score_pixel(a, s_op, j, s_o, fn, nullptr, &al, &co)) continue;
           double gg = gain_of(s_op, fn, f);
-          if (better(gg, j, g, pix)) { g = gg; pix = j; }
+          if (better(gg, j, g, pix)) {
+            g = gg;
+            pix = j;
+            b_alpha = al;
+            b_coef = co;
+          }
         }
       }
       CandRecord* rc = rec_at(a, slot, cta);
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
         long long bmin = block_min_ll(best);
-        if (threadIdx.x == 0) a.part_key[slot * P + cta] = bmin;
+        if (threadIdx.x == 0) sel_offer(ctl, rd, bmin, cta);
         if (bmin == LLONG_MAX) {
           if (threadIdx.x == 0) rc->key = LLONG_MAX;
         } else if (best == bmin) {
-          fill_record(a, rc, pix, best, 0.0);
+          fill_record(a, rc, pix, best, 0.0, b_alpha, b_coef);
         }
       } else {
         double gb = g;
@@ -251,32 +310,34 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         if (pb2 == INT_MAX) {
           if (threadIdx.x == 0) { rc->key = LLONG_MAX; rc->gain = -INFINITY; rc->pixel = INT_MAX; }
         } else if (pix == pb2) {
-          fill_record(a, rc, pix, 0, gb);
+          fill_record(a, rc, pix, 0, gb, b_alpha, b_coef);
         }
       }
     }
     tick(0);
     if (!grid_sync(ctl)) { failed = true; break; }
     tick(1);
-    // ---- warp 0 picks the winning record; lane 0 forms the pivot
+    // ---- warp 0 picks the winning record; lane 0 forms the pivot while the
+    //      other lanes already gather beta_i = alpha_i x_i[k] (FIRST mode: k is
+    //      known from the selection cell before the record arrives)
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      int win = -1;
+      int win = -1, k_pre = -1;
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-        long long best = LLONG_MAX;
-        int q_best = -1;
-        const long long* keys = a.part_key + slot * P;
-#pragma unroll 8
-        for (int q = lane; q < P; q += 32) {
-          long long kq = keys[q];
-          if (kq < best) { best = kq; q_best = q; }
+        unsigned long long key = sel_read(ctl, rd);
+        if (key != ~0ull) {
+          win = (int)(key & 1023u);
+          int pos = (int)(key >> 10);
+          k_pre = a.order ? a.order[(size_t)s * n + pos] : pos;
+          if ((unsigned)k_pre < (unsigned)n) {
+            for (int i = lane; i < r; i += 32) {
+              c128 al = a.xa[i];
+              float2 x = a.X[(size_t)k_pre * a.R + i];
+              float ax = (float)al.x, ay = (float)al.y;
+              s_beta[i] = make_float2(fmaf(ax, x.x, -ay * x.y), fmaf(ax, x.y, ay * x.x));
+            }
+          }
         }
-        for (int off = 16; off > 0; off >>= 1) {
-          long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-          int oq = __shfl_xor_sync(0xffffffffu, q_best, off);
-          if (ob < best || (ob == best && oq < q_best)) { best = ob; q_best = oq; }
-        }
-        if (best != LLONG_MAX) win = q_best;
       } else {
         double g = -INFINITY;
         int pix = INT_MAX, q_best = -1;
@@ -306,9 +367,21 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           s_f = objective_of(s_op, s_o);
         }
       }
+      if (a.mode == PNGF_BEST_IMPROVEMENT) {
+        __syncwarp();
+        const int kb = s_k;
+        if (kb >= 0)
+          for (int i = lane; i < r; i += 32) {
+            c128 al = a.xa[i];
+            float2 x = a.X[(size_t)kb * a.R + i];
+            float ax = (float)al.x, ay = (float)al.y;
+            s_beta[i] = make_float2(fmaf(ax, x.x, -ay * x.y), fmaf(ax, x.y, ay * x.x));
+          }
+      }
     }
     __syncthreads();
     slot ^= 1;
+    ++rd;
     const int k = s_k, pos_k = s_pos;
     if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) {
       status = PNGF_EINVAL;
@@ -362,9 +435,6 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       a.xa[r] = s_pv.alpha;
     }
     ++n_acc;
-    // beta_i = alpha_i x_i[k] for the delayed columns
-    for (int i = threadIdx.x; i < r; i += blockDim.x) s_beta[i] = cmul(a.xa[i], a.X[(size_t)k * a.R + i]);
-    __syncthreads();
     tick(2);
     mixed_accept_own(a, s_pv, s_beta, r, pb, pe);
     ++r;
@@ -379,12 +449,16 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         ++n_refresh;
         refresh_x(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
+        tick(8);
         refresh_residual(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
+        tick(9);
         refresh_correct(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
+        tick(10);
         ports_partial(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
+        tick(11);
         if (threadIdx.x == 0) {
           FOR_PORTS(p, a.n_o) {
             c128 acc = mk(0.0, 0.0);
@@ -428,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     ctl->counters[6] = status;
     ctl->counters[7] = 0;
     ph[7] = clock64() - t_begin;
-    for (int q = 0; q < 8; ++q) ctl->phase_cycles[q] = ph[q];
+    for (int q = 0; q < 16; ++q) ctl->phase_cycles[q] = ph[q];
     if (a.counters)
       for (int q = 0; q < 8; ++q) a.counters[q] = ctl->counters[q];
     if (status == PNGF_ENUMERIC || status == PNGF_ETIMEOUT || status == PNGF_EINVAL) latch_status(ctl, status);
@@ -449,7 +523,7 @@ __global__ void to_planar_fp32(const c128* __restrict__ W, int n, int ldw, float
 // ---------------------------------------------------------------- single calls
 __global__ void mixed_accept_kernel(SweepArgs a, int k) {
   __shared__ Pivot s_pv;
-  __shared__ c128 s_beta[kMaxDelay];
+  __shared__ float2 s_beta[kMaxDelay];
   __shared__ int s_r;
   // every CTA rebuilds the pivot from the state of pixel k, which only the
   // owner of k changes, after all CTAs have read it: pixel k's state is read
@@ -461,7 +535,7 @@ __global__ void mixed_accept_kernel(SweepArgs a, int k) {
   }
   __syncthreads();
   const int r = s_r;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) s_beta[i] = cmul(a.xa[i], a.X[(size_t)k * a.R + i]);
+  make_beta(a, k, r, s_beta);
   __syncthreads();
   const int P = gridDim.x, n = a.n;
   const int pb = (int)((long long)n * blockIdx.x / P), pe = (int)((long long)n * (blockIdx.x + 1) / P);
@@ -471,7 +545,7 @@ __global__ void mixed_accept_kernel(SweepArgs a, int k) {
 __global__ void accept_snapshot_kernel(SweepArgs a, int k) {
   if (threadIdx.x == 0) {
     CandRecord* rk = reinterpret_cast<CandRecord*>(a.rec);
-    fill_record(a, rk, k, 0, 0.0);
+    fill_record_from_state(a, rk, k);
     Pivot pv;
     pivot_from_record(*rk, a.n_o, pv);
     c128 o[kMaxPorts];
@@ -504,7 +578,7 @@ __global__ void flush_reset_kernel(SweepArgs a) {
   if (threadIdx.x == 0 && a.ctl->r_delay >= a.R) a.ctl->r_delay = 0;
 }
 
-constexpr size_t kFlushSmem = 2 * FT * kMaxDelay * sizeof(f2x);
+constexpr size_t kFlushSmem = 2 * (FT + 1) * kMaxDelay * sizeof(f2x);
 
 }  // namespace
 
@@ -544,6 +618,8 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   a.counters = counters;
   Control* ctl = a.ctl;
   cudaError_t err = cudaMemsetAsync(&ctl->bar_count, 0, 2 * sizeof(unsigned), c->stream);
+  if (err != cudaSuccess) return PNGF_ECUDA;
+  err = cudaMemsetAsync(&ctl->sel[0], 0xff, sizeof(ctl->sel), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
   int grid = mixed_grid(c);
   void* params[] = {&a};

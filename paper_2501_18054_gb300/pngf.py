@@ -175,7 +175,7 @@ def pngf_restore(ctx: int) -> None:
 
 
 def pngf_get_phase_cycles(ctx: int) -> np.ndarray:
-    out = (ctypes.c_int64 * 8)()
+    out = (ctypes.c_int64 * 16)()
     _check(lib().pngf_get_phase_cycles(ctx, ctypes.cast(out, _P)), "pngf_get_phase_cycles")
     return np.frombuffer(out, dtype=np.int64).copy()
 
