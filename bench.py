@@ -197,6 +197,127 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched workload
+BATCH_WORKLOAD = "batch256_fdfd128_metal"  # 256 runs, N_d in {256, 576, 1024} sub-blocks of one G
+
+
+def batch_cases(Wl):
+    """The batched workload: random starts b = 0..255 on the 128^2 lossy-metal device.
+
+    Run b uses the principal sub-block [256, 576, 1024][b % 3] of the 32 x 32
+    design region (16 x 16 at offset (8, 8), 24 x 24 at (4, 4), the whole
+    region), seed b; the three sub-block Green functions are shared.
+    """
+    big = Wl.get_case("fdfd128_metal")
+
+    def block(x0, side):
+        return np.array([(x0 + i) * 32 + (x0 + j) for i in range(side) for j in range(side)])
+
+    subs = [big.sub_case(block(8, 16), "metal_sub256"), big.sub_case(block(4, 24), "metal_sub576"), big]
+    return [(subs[b % 3], b) for b in range(256)]
+
+
+def bench_batch(args, torch, dist, dev, P, Wl):
+    runs = batch_cases(Wl)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        shared = {}
+        ctxs = []
+        t_f0 = time.perf_counter()
+        for case, seed in runs:
+            if case.name not in shared:
+                c0 = P.DbsContext(case, precision=P.PNGF_FP64, tau=args.tau, refresh_k=args.refresh_k,
+                                  device=str(dev), stream=stream)
+                shared[case.name] = (c0.G, c0.God, c0.cd, c0.co, c0.dv)
+                ctx = c0
+            else:
+                ctx = P.DbsContext(case, precision=P.PNGF_FP64, tau=args.tau, refresh_k=args.refresh_k,
+                                   device=str(dev), stream=stream, inputs_on_device=shared[case.name])
+            ctx.factor(Wl.random_design(case.n_d, seed + 1000 * dist.rank))
+            ctxs.append(ctx)
+        stream.synchronize()
+        factor_s = time.perf_counter() - t_f0
+        for c in ctxs:
+            if c.sync() != 0:
+                raise RuntimeError("factor failed")
+            c.snapshot()
+        batch = P.DbsBatch(ctxs)
+        trace_cap = args.sweeps * 1024
+        traces = [torch.zeros((trace_cap, 4), dtype=torch.int32, device=dev) for _ in ctxs]
+        counters = batch.counters
+
+        def step():
+            for c in ctxs:
+                P.pngf_restore(c.ctx)
+            P.pngf_dbs_sweep_batch([c.ctx for c in ctxs], args.sweeps, None, [t.data_ptr() for t in traces], None,
+                                   trace_cap, counters.data_ptr(), batch.ws.data_ptr(), batch.ws_bytes)
+
+        for _ in range(max(args.warmup, 1)):
+            step()
+        stream.synchronize()
+        cnt = counters.cpu().numpy().copy()
+        evals = int(cnt[:, 1].sum())
+        peak_fp64 = fp64_peak_gflops(stream.cuda_stream)
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = Clocks(dist.local)
+        clocks.start()
+        time.sleep(0.3)
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            for c in ctxs:
+                P.pngf_restore(c.ctx)
+            kev[i][0].record(stream)
+            P.pngf_dbs_sweep_batch([c.ctx for c in ctxs], args.sweeps, None, [t.data_ptr() for t in traces], None,
+                                   trace_cap, counters.data_ptr(), batch.ws.data_ptr(), batch.ws_bytes)
+            kev[i][1].record(stream)
+        t1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        dist.barrier()
+        for c in ctxs:
+            if c.sync() != 0:
+                raise RuntimeError("batched steps failed")
+        cnt2 = counters.cpu().numpy()
+        assert int(cnt2[:, 1].sum()) == evals
+        ms = t0.elapsed_time(t1)
+        ms_max = dist.max(torch, ms, dev)
+        total = dist.sum(torch, float(evals * args.steps), dev)
+        value = total / (ms_max / 1e3)
+        k_avg = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+        # algorithmic FP64 work of the batched kernel per launch: the rank-1 update of
+        # the upper triangle per kept flip (8 flop per element) plus per refresh the
+        # FP64 residual G x over (1 + n_o) vectors (8 flop per complex multiply-add)
+        flops = 0.0
+        for (case, _), row in zip(runs, cnt2):
+            n = case.n_d
+            flops += row[0] * 8.0 * n * (n + 1) / 2 + row[4] * 8.0 * n * n * (1 + case.n_o)
+        gf = flops / (k_avg / 1e3) / 1e9
+        roofline = {"bound": "alu", "achieved": gf / 1e3, "peak": peak_fp64 / 1e3, "unit": "TFLOP/s",
+                    "frac": gf / peak_fp64, "traffic": None, "kernel": "dbs_batch_kernel",
+                    "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks"}
+    if dist.rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=dist.world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f64", data="synthetic",
+                    config={"workload": BATCH_WORKLOAD, "runs": len(runs), "n_d": "256/576/1024 (b mod 3)",
+                            "precision": "fp64", "mode": "first-improvement, raster order",
+                            "max_sweeps": args.sweeps, "refresh_k": args.refresh_k, "tau": args.tau,
+                            "step": "restore every run's factored start + one batched launch to convergence",
+                            "l2": "inputs larger than L2 (W of all runs ~%.1f GB)" % (
+                                sum(c.n_d ** 2 for c, _ in runs) * 16 / 1e9)},
+                    roofline=roofline, cpu_baseline=None, e2e=None, clocks=clk, gpu_launches=args.steps,
+                    evals_per_step=evals, accepts_per_step=int(cnt2[:, 0].sum()),
+                    converged_runs=int(cnt2[:, 3].sum()), kernel_ms_avg=k_avg, factor_s_all_runs=factor_s,
+                    fp64_peak_gflops=peak_fp64)
+        print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -216,6 +337,8 @@ def main():
     from paper_2501_18054_gb300 import pngf as P
     from paper_2501_18054_gb300 import workloads as Wl
 
+    if args.workload == BATCH_WORKLOAD:
+        return bench_batch(args, torch, dist, dev, P, Wl)
     case = Wl.get_case(case_name(args.workload))
     n, n_o = case.n_d, case.n_o
     prec = P.PNGF_MIXED if args.precision == "mixed" else P.PNGF_FP64

@@ -185,6 +185,32 @@ pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order
                            int32_t* trace, double* trace_f, int32_t trace_cap,
                            int64_t* counters);
 
+/*
+ * Batched DBS: many independent runs advanced by one kernel launch, one CTA
+ * per run at a time.  Independent systems need no communication (the paper
+ * updates its per-frequency systems "in parallel without any communication
+ * overhead", section "Computational efficiency"); here they are independent
+ * random starts and/or design regions of different sizes sharing one device.
+ *   ctxs      host array of n_ctx factored contexts (1 <= n_ctx <= PNGF_BATCH_MAX_RUNS),
+ *             one device, one precision and mode, n_d <= PNGF_BATCH_MAX_ND each;
+ *             the launch goes to ctxs[0]'s stream, which must order every
+ *             context's earlier work
+ *   orders    host array of n_ctx device pointers (each as pngf_dbs_sweep's
+ *             order, NULL = raster), or NULL for raster everywhere
+ *   traces, trace_f   host arrays of n_ctx device pointers, or NULL
+ *   trace_cap capacity of every trace
+ *   counters  int64 n_ctx x 8 (device, out), per run as in pngf_dbs_sweep
+ *   batch_ws  device scratch of pngf_batch_workspace_size(n_ctx) bytes, 256-byte aligned
+ * Each run follows the same semantics as pngf_dbs_sweep on its own context.
+ */
+#define PNGF_BATCH_MAX_RUNS 65536
+#define PNGF_BATCH_MAX_ND 4096
+pngf_status pngf_batch_workspace_size(int32_t n_ctx, size_t* bytes);
+pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n_sweeps,
+                                 const int32_t* const* orders, int32_t* const* traces,
+                                 double* const* trace_f, int32_t trace_cap, int64_t* counters,
+                                 void* batch_ws, size_t batch_ws_bytes);
+
 /* Current port amplitudes (c128 n_o, host) and objective (host); synchronizes. */
 pngf_status pngf_eval_ports(pngf_ctx* ctx, double* o_host, double* f_host);
 

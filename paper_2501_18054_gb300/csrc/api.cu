@@ -184,6 +184,33 @@ pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, 
   return run_sweep(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
 }
 
+pngf_status pngf_batch_workspace_size(int32_t n_ctx, size_t* bytes) {
+  if (n_ctx < 1 || n_ctx > PNGF_BATCH_MAX_RUNS || !bytes) return PNGF_EINVAL;
+  *bytes = batch_workspace_bytes(n_ctx);
+  return PNGF_OK;
+}
+
+pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n_sweeps,
+                                 const int32_t* const* orders, int32_t* const* traces, double* const* trace_f,
+                                 int32_t trace_cap, int64_t* counters, void* batch_ws, size_t batch_ws_bytes) {
+  if (!ctxs || n_ctx < 1 || n_ctx > PNGF_BATCH_MAX_RUNS || n_sweeps < 0 || trace_cap < 0 || !batch_ws)
+    return PNGF_EINVAL;
+  if (batch_ws_bytes < batch_workspace_bytes(n_ctx)) return PNGF_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(batch_ws) % 256 != 0) return PNGF_EINVAL;
+  const pngf_ctx* c0 = ctxs[0];
+  if (!c0) return PNGF_EINVAL;
+  for (int r = 0; r < n_ctx; ++r) {
+    const pngf_ctx* c = ctxs[r];
+    if (!c) return PNGF_EINVAL;
+    if (!c->factored) return PNGF_ENOTFACTORED;
+    if (c->cfg.precision != c0->cfg.precision || c->cfg.mode != c0->cfg.mode) return PNGF_EINVAL;
+    if (c->cfg.n_d > PNGF_BATCH_MAX_ND || c->device != c0->device) return PNGF_EINVAL;
+  }
+  if (n_sweeps == 0) return PNGF_OK;
+  return run_sweep_batch(ctxs, n_ctx, n_sweeps, orders, traces, trace_f, trace_cap, counters, batch_ws,
+                         batch_ws_bytes);
+}
+
 pngf_status pngf_eval_ports(pngf_ctx* c, double* o_host, double* f_host) {
   if (!c) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;

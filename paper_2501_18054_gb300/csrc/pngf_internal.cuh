@@ -159,6 +159,11 @@ pngf_status mixed_after_factor(pngf_ctx* c);
 pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace,
                             double* trace_f, int32_t trace_cap, int64_t* counters);
 pngf_status accept_flip_mixed(pngf_ctx* c, int pixel);
+// batch.cu
+size_t batch_workspace_bytes(int n_runs);
+pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, const int32_t* const* orders,
+                            int32_t* const* traces, double* const* trace_f, int32_t trace_cap, int64_t* counters,
+                            void* ws, size_t ws_bytes);
 // sweep.cu
 pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace,
                       double* trace_f, int32_t trace_cap, int64_t* counters);

@@ -26,6 +26,8 @@ PNGF_FIRST_IMPROVEMENT, PNGF_BEST_IMPROVEMENT = 0, 1
 PNGF_OBJ_MAX_WEIGHTED_POWER, PNGF_OBJ_MIN_INSERTION_LOSS = 0, 1
 PNGF_MAX_PORTS = 8
 PNGF_NOALLOC_MAX_ND = 8192
+PNGF_BATCH_MAX_RUNS = 65536
+PNGF_BATCH_MAX_ND = 4096
 
 
 class pngf_config(ctypes.Structure):
@@ -73,6 +75,9 @@ def lib() -> ctypes.CDLL:
             "pngf_accept_flip": (st, [_P, ctypes.c_int32]),
             "pngf_accept_flip_noalloc": (st, [_P, ctypes.c_int32]),
             "pngf_dbs_sweep": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]),
+            "pngf_batch_workspace_size": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+            "pngf_dbs_sweep_batch": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, _P,
+                                          ctypes.c_size_t]),
             "pngf_eval_ports": (st, [_P, _P, _P]),
             "pngf_get_design": (st, [_P, _P]),
             "pngf_get_state": (st, [_P, _P, _P, _P, _P, _P]),
@@ -96,7 +101,7 @@ def exported_symbols() -> list:
     L = lib()
     names = []
     for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
-              "pngf_accept_flip_noalloc",
+              "pngf_accept_flip_noalloc", "pngf_batch_workspace_size", "pngf_dbs_sweep_batch",
               "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state", "pngf_snapshot",
               "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
         if hasattr(L, n):
@@ -147,6 +152,31 @@ def pngf_accept_flip_noalloc(ctx: int, pixel: int) -> None:
 def pngf_dbs_sweep(ctx: int, n_sweeps: int, order: Optional[int], trace: Optional[int],
                    trace_f: Optional[int], trace_cap: int, counters: Optional[int]) -> None:
     _check(lib().pngf_dbs_sweep(ctx, n_sweeps, order, trace, trace_f, trace_cap, counters), "pngf_dbs_sweep")
+
+
+def pngf_batch_workspace_size(n_ctx: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().pngf_batch_workspace_size(int(n_ctx), ctypes.byref(out)), "pngf_batch_workspace_size")
+    return int(out.value)
+
+
+def _ptr_array(ptrs):
+    if ptrs is None:
+        return None
+    arr = (ctypes.c_void_p * len(ptrs))(*[p if p else None for p in ptrs])
+    return arr
+
+
+def pngf_dbs_sweep_batch(ctxs, n_sweeps: int, orders, traces, trace_f, trace_cap: int, counters: Optional[int],
+                         batch_ws: int, batch_ws_bytes: int) -> None:
+    h = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    o, t, tf = _ptr_array(orders), _ptr_array(traces), _ptr_array(trace_f)
+    _check(lib().pngf_dbs_sweep_batch(ctypes.cast(h, _P), len(ctxs), int(n_sweeps),
+                                      ctypes.cast(o, _P) if o is not None else None,
+                                      ctypes.cast(t, _P) if t is not None else None,
+                                      ctypes.cast(tf, _P) if tf is not None else None,
+                                      int(trace_cap), counters, batch_ws, int(batch_ws_bytes)),
+           "pngf_dbs_sweep_batch")
 
 
 def pngf_eval_ports(ctx: int, n_o: int):
@@ -334,3 +364,47 @@ class DbsContext:
             self.close()
         except Exception:
             pass
+
+
+class DbsBatch:
+    """Many independent runs (one DbsContext each) advanced by one launch."""
+
+    def __init__(self, contexts):
+        import torch
+
+        self.torch = torch
+        self.ctxs = list(contexts)
+        c0 = self.ctxs[0]
+        self.device = c0.device
+        self.stream = c0.stream
+        self.ws_bytes = pngf_batch_workspace_size(len(self.ctxs))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.counters = torch.zeros((len(self.ctxs), 8), dtype=torch.int64, device=self.device)
+
+    def dbs_sweep(self, n_sweeps: int, orders=None, trace_cap: Optional[int] = None, sync: bool = True):
+        torch = self.torch
+        if trace_cap is None:
+            trace_cap = max(1, n_sweeps * max(c.n_d for c in self.ctxs))
+        self.traces = [torch.zeros((trace_cap, 4), dtype=torch.int32, device=self.device) for _ in self.ctxs]
+        self.trace_fs = [torch.zeros(trace_cap, dtype=torch.float64, device=self.device) for _ in self.ctxs]
+        od = None
+        if orders is not None:
+            self._orders_keep = [None if o is None else torch.as_tensor(np.ascontiguousarray(o, dtype=np.int32)).to(
+                self.device) for o in orders]
+            od = [0 if o is None else o.data_ptr() for o in self._orders_keep]
+        pngf_dbs_sweep_batch([c.ctx for c in self.ctxs], n_sweeps, od, [t.data_ptr() for t in self.traces],
+                             [t.data_ptr() for t in self.trace_fs], trace_cap, self.counters.data_ptr(),
+                             self.ws.data_ptr(), self.ws_bytes)
+        if not sync:
+            return None
+        for c in self.ctxs:
+            st = c.sync()
+            if st != PNGF_OK:
+                raise PngfError(st, "pngf_dbs_sweep_batch")
+        cnt = self.counters.cpu().numpy()
+        out = []
+        for i, c in enumerate(self.ctxs):
+            n_acc = int(min(cnt[i, 0], trace_cap))
+            out.append(dict(trace=self.traces[i][:n_acc].cpu().numpy(), trace_f=self.trace_fs[i][:n_acc].cpu().numpy(),
+                            counters=cnt[i]))
+        return out
