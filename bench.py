@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--delay-r", type=int, default=64)
+    ap.add_argument("--tensor-fold", type=int, default=1, choices=[0, 1],
+                    help="mixed path: fold the delayed set with tcgen05 (1) or FP32 CUDA cores (0)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--refresh-k", type=int, default=64)
@@ -345,7 +347,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         ctx = P.DbsContext(case, precision=prec, tau=args.tau, refresh_k=args.refresh_k, delay_r=args.delay_r,
-                           device=str(dev), stream=stream)
+                           device=str(dev), stream=stream, tensor_fold=args.tensor_fold)
         b0 = Wl.random_design(n, seed=dist.rank)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -546,6 +548,8 @@ def main():
                     "mode": "first-improvement, raster order", "max_sweeps": args.sweeps,
                     "refresh_k": args.refresh_k, "tau": args.tau,
                     "delay_r": args.delay_r if prec == P.PNGF_MIXED else None,
+                    "fold": ("tcgen05 3xTF32" if args.tensor_fold else "FP32 CUDA cores")
+                    if prec == P.PNGF_MIXED else None,
                     "step": "restore factored start state + DBS run to convergence",
                     "l2": "inputs larger than L2 (W = %.0f MB complex128)" % (n * n * 16 / 1e6),
                     "replicas": "one independent run per GPU (seed = rank)"},

@@ -94,6 +94,9 @@ typedef struct {
   double obj_weights[PNGF_MAX_PORTS]; /* w_p */
   double s_off[2 * PNGF_MAX_PORTS];   /* c128 per port */
   double s_scale[2 * PNGF_MAX_PORTS]; /* c128 per port */
+  int32_t tensor_fold; /* PNGF_MIXED: 1 = fold the delayed set into the FP32 inverse on the
+                          tensor cores (tcgen05, 3xTF32), 0 = FP32 CUDA cores */
+  int32_t reserved;
 } pngf_config;
 
 /* Bytes of device workspace a context with this configuration needs. */

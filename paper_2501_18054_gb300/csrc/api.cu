@@ -6,7 +6,7 @@
 #include <cstring>
 #include <new>
 
-#include "pngf_internal.cuh"
+#include "flush_tc.cuh"
 
 namespace pngf {
 
@@ -52,6 +52,12 @@ Layout make_layout(const pngf_config& cfg) {
   L.pos_of = take(n * sizeof(int));
   L.part = take((size_t)L.n_part * (2 * sizeof(long long) + 2 * sizeof(double) + kMaxPorts * c));
   L.rec = take((size_t)2 * L.n_part * 256);
+  if (mixed) {
+    const size_t nk = (size_t)(L.R + TC_KC - 1) / TC_KC;
+    L.tcimgA_bytes = (size_t)((n + TC_M - 1) / TC_M) * nk * TC_ACHUNK;
+    L.tcimg_bytes = tc_image_bytes((int)n, L.R);
+  }
+  L.tcimg = take(L.tcimg_bytes);
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
   L.ipiv = take(2 * n * sizeof(int));
@@ -204,6 +210,7 @@ pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n
     if (!c) return PNGF_EINVAL;
     if (!c->factored) return PNGF_ENOTFACTORED;
     if (c->cfg.precision != c0->cfg.precision || c->cfg.mode != c0->cfg.mode) return PNGF_EINVAL;
+    if (c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold != c0->cfg.tensor_fold) return PNGF_EINVAL;
     if (c->cfg.n_d > PNGF_BATCH_MAX_ND || c->device != c0->device) return PNGF_EINVAL;
   }
   if (n_sweeps == 0) return PNGF_OK;

@@ -17,7 +17,7 @@
 #include <cstdio>
 #include <vector>
 
-#include "mixed_common.cuh"
+#include "flush_tc.cuh"
 
 namespace pngf {
 namespace {
@@ -70,7 +70,25 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   __shared__ float2 s_beta[kMaxDelay];
   __shared__ int s_k;
   __shared__ long long s_best;
-  for (int run = blockIdx.x; run < n_runs; run += gridDim.x) {
+  // tensor-core fold: this CTA holds TC_TMEM_COLS columns of tensor memory for all its runs
+  __shared__ __align__(8) unsigned long long s_mb_load, s_mb_mma;
+  __shared__ unsigned s_tmem;
+  const bool use_tc = n_runs > 0 && runs[0].tensor_fold;
+  TcState tcs;
+  tcs.tmem = 0;
+  tcs.ph_load = tcs.ph_mma = 0;
+  if (use_tc) {
+    tc_mbar_init(&s_mb_load, &s_mb_mma);
+    tc_alloc(&s_tmem);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tcs.tmem = s_tmem;
+    tcs.mb_load = (unsigned)__cvta_generic_to_shared(&s_mb_load);
+    tcs.mb_mma = (unsigned)__cvta_generic_to_shared(&s_mb_mma);
+  }
+  bool tc_failed = false;
+  for (int run = blockIdx.x; run < n_runs && !tc_failed; run += gridDim.x) {
     const SweepArgs& a = runs[run];
     const int n = a.n;
     Control* ctl = a.ctl;
@@ -229,7 +247,18 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
         ++since_refresh;
         if (r == a.R) {
           __syncthreads();
-          flush_tiles(a, r, reinterpret_cast<float*>(dyn), 0, 1);
+          if (use_tc) {
+            tc_prepare(a, r, a.tcimgA, a.tcimgB, threadIdx.x, blockDim.x);
+            __threadfence_block();
+            __syncthreads();
+            if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, dyn, tcs, 0, 1)) {
+              status = PNGF_ETIMEOUT;
+              tc_failed = true;
+              break;
+            }
+          } else {
+            flush_tiles(a, r, reinterpret_cast<float*>(dyn), 0, 1);
+          }
           __syncthreads();
           r = 0;
           ++n_flush;
@@ -264,8 +293,17 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
       for (int q = 0; q < 8; ++q) ctl->counters[q] = cnt[q];
       if (a.counters)
         for (int q = 0; q < 8; ++q) a.counters[q] = cnt[q];
-      if (status == PNGF_ENUMERIC || status == PNGF_EINVAL) latch_status(ctl, status);
+      if (status == PNGF_ENUMERIC || status == PNGF_EINVAL || status == PNGF_ETIMEOUT) latch_status(ctl, status);
     }
+  }
+  if (use_tc) {
+    if (tc_failed && threadIdx.x < 128) {
+      mbar_wait(tcs.mb_load, tcs.ph_load);
+      mbar_wait(tcs.mb_mma, tcs.ph_mma);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    tc_free(tcs.tmem);
   }
 }
 
@@ -294,7 +332,7 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
       cudaSuccess)
     return PNGF_ECUDA;
   const bool mixed = c0->cfg.precision == PNGF_MIXED;
-  size_t smem = mixed ? kFlushSmem : (size_t)max_n * sizeof(c128);
+  size_t smem = mixed ? (kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM) : (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PNGF_ECUDA;
   int per_sm = 0;

@@ -119,6 +119,7 @@ struct Layout {
   size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, cbuf, ipiv, rbuf,
       snapW, snapState, ctl, total;
   size_t snapW_bytes;  // bytes of the maintained inverse copied by snapshot
+  size_t tcimg, tcimgA_bytes, tcimg_bytes;  // mixed path: operand images of the tensor-core fold
   int ldw, ldl, ldt, R, n_part;
   size_t state_bytes;  // contiguous state block [diag .. b] copied by snapshot
 };
@@ -159,6 +160,8 @@ pngf_status mixed_after_factor(pngf_ctx* c);
 pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace,
                             double* trace_f, int32_t trace_cap, int64_t* counters);
 pngf_status accept_flip_mixed(pngf_ctx* c, int pixel);
+// flush_tc.cu
+pngf_status flush_tc_launch(pngf_ctx* c);
 // batch.cu
 size_t batch_workspace_bytes(int n_runs);
 pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, const int32_t* const* orders,

@@ -39,6 +39,9 @@ struct SweepArgs {
   ObjParams op;
   // mixed path
   int mixed, ldl, R;
+  int tensor_fold;        // mixed: fold the delayed set on the tensor cores
+  unsigned char* tcimgA;  // operand images of the tensor-core fold
+  unsigned char* tcimgB;
   float* Wr;  // planar FP32 copy of W (upper triangle current)
   float* Wi;
   float2* X;  // n x R delayed columns c_i in FP32 (row j holds c_0[j] .. c_{R-1}[j])
@@ -539,6 +542,9 @@ SweepArgs make_args(pngf_ctx* c) {
   a.X = at<float2>(c, L.X);
   a.xa = at<c128>(c, L.xa);
   a.rec = c->ws + L.rec;
+  a.tensor_fold = c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold;
+  a.tcimgA = reinterpret_cast<unsigned char*>(c->ws) + L.tcimg;
+  a.tcimgB = a.tcimgA + L.tcimgA_bytes;
   return a;
 }
 

@@ -20,7 +20,7 @@
 // state arrays of the chosen pixel while its owner updates them.
 #include <cstdio>
 
-#include "mixed_common.cuh"
+#include "flush_tc.cuh"
 
 namespace pngf {
 namespace {
@@ -68,9 +68,36 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         else latch_status(ctl, PNGF_EINVAL);
       }
   };
+  // tensor-core fold: warp 0 holds TC_TMEM_COLS columns of tensor memory for the whole search
+  __shared__ __align__(8) unsigned long long s_mb_load, s_mb_mma;
+  __shared__ unsigned s_tmem;
+  TcState tcs;
+  tcs.tmem = 0;
+  tcs.ph_load = tcs.ph_mma = 0;
+  if (a.tensor_fold) {
+    tc_mbar_init(&s_mb_load, &s_mb_mma);
+    tc_alloc(&s_tmem);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tcs.tmem = s_tmem;
+    tcs.mb_load = (unsigned)__cvta_generic_to_shared(&s_mb_load);
+    tcs.mb_mma = (unsigned)__cvta_generic_to_shared(&s_mb_mma);
+  }
   auto flush = [&]() -> bool {
     if (!grid_sync(ctl)) return false;
-    flush_tiles(a, r, dyn_smem, blockIdx.x, gridDim.x);
+    if (a.tensor_fold) {
+      tc_prepare(a, r, a.tcimgA, a.tcimgB, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x);
+      if (!grid_sync(ctl)) return false;
+      if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, reinterpret_cast<unsigned char*>(dyn_smem), tcs, blockIdx.x,
+                         gridDim.x)) {
+        if (threadIdx.x == 0) latch_status(ctl, PNGF_ETIMEOUT);
+        return false;
+      }
+    } else {
+      flush_tiles(a, r, dyn_smem, blockIdx.x, gridDim.x);
+    }
     if (!grid_sync(ctl)) return false;
     r = 0;
     ++n_flush;
@@ -306,6 +333,16 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       }
     }
   }
+  if (a.tensor_fold) {
+    if (failed && threadIdx.x < 128) {
+      // give what this CTA issued a bounded time to land before the free
+      mbar_wait(tcs.mb_load, tcs.ph_load);
+      mbar_wait(tcs.mb_mma, tcs.ph_mma);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    tc_free(tcs.tmem);
+  }
   if (cta == 0 && threadIdx.x == 0) {
     if (failed) status = PNGF_ETIMEOUT;
     FOR_PORTS(p, a.n_o) ctl->o[p] = s_o[p];
@@ -409,15 +446,17 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
+constexpr size_t kMixedSmem = kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM;
+
 static int mixed_grid(pngf_ctx* c) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(dbs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
+    cudaFuncSetAttribute(dbs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedSmem);
     cudaFuncSetAttribute(flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
     attr = true;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_mixed_kernel, kThreads, kFlushSmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_mixed_kernel, kThreads, kMixedSmem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;
   int g = c->n_sm * per_sm;
@@ -442,7 +481,7 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   if (err != cudaSuccess) return PNGF_ECUDA;
   int grid = mixed_grid(c);
   void* params[] = {&a};
-  err = cudaLaunchCooperativeKernel((const void*)dbs_mixed_kernel, dim3(grid), dim3(kThreads), params, kFlushSmem,
+  err = cudaLaunchCooperativeKernel((const void*)dbs_mixed_kernel, dim3(grid), dim3(kThreads), params, kMixedSmem,
                                     c->stream);
   return cuda_status(err);
 }
@@ -453,7 +492,12 @@ pngf_status accept_flip_mixed(pngf_ctx* c, int pixel) {
   accept_snapshot_kernel<<<1, 32, 0, c->stream>>>(a, pixel);
   mixed_accept_kernel<<<c->n_sm, kThreads, 0, c->stream>>>(a, pixel);
   accept_finish_kernel<<<1, 32, 0, c->stream>>>(a);
-  flush_kernel<<<c->n_sm, kThreads, kFlushSmem, c->stream>>>(a);
+  if (c->cfg.tensor_fold) {
+    pngf_status st = flush_tc_launch(c);
+    if (st != PNGF_OK) return st;
+  } else {
+    flush_kernel<<<c->n_sm, kThreads, kFlushSmem, c->stream>>>(a);
+  }
   flush_reset_kernel<<<1, 32, 0, c->stream>>>(a);
   return cuda_status(cudaGetLastError());
 }

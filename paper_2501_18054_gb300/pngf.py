@@ -44,6 +44,8 @@ class pngf_config(ctypes.Structure):
         ("obj_weights", ctypes.c_double * PNGF_MAX_PORTS),
         ("s_off", ctypes.c_double * (2 * PNGF_MAX_PORTS)),
         ("s_scale", ctypes.c_double * (2 * PNGF_MAX_PORTS)),
+        ("tensor_fold", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -221,11 +223,13 @@ def pngf_destroy(ctx: int) -> None:
 # ---------------------------------------------------------------- convenience wrapper
 def make_config(n_d: int, n_o: int, *, precision: int = PNGF_FP64, mode: int = PNGF_FIRST_IMPROVEMENT,
                 objective: int = PNGF_OBJ_MAX_WEIGHTED_POWER, refresh_k: int = 64, delay_r: int = 64,
-                n_ctas: int = 0, tau: float = 1e-9, obj_weights=None, s_off=None, s_scale=None) -> pngf_config:
+                n_ctas: int = 0, tau: float = 1e-9, obj_weights=None, s_off=None, s_scale=None,
+                tensor_fold: int = 0) -> pngf_config:
     cfg = pngf_config()
     cfg.n_d, cfg.n_o = int(n_d), int(n_o)
     cfg.precision, cfg.mode, cfg.objective = int(precision), int(mode), int(objective)
     cfg.refresh_k, cfg.delay_r, cfg.n_ctas, cfg.tau = int(refresh_k), int(delay_r), int(n_ctas), float(tau)
+    cfg.tensor_fold = int(tensor_fold)
     w = np.zeros(PNGF_MAX_PORTS)
     if obj_weights is not None:
         w[:n_o] = np.asarray(obj_weights, dtype=np.float64)[:n_o]
@@ -247,7 +251,7 @@ class DbsContext:
 
     def __init__(self, case, *, precision: int = PNGF_FP64, mode: int = PNGF_FIRST_IMPROVEMENT,
                  tau: float = 1e-9, refresh_k: int = 64, delay_r: int = 64, n_ctas: int = 0,
-                 device: str = "cuda", stream=None, inputs_on_device=None):
+                 device: str = "cuda", stream=None, inputs_on_device=None, tensor_fold: int = 0):
         import torch
 
         self.torch = torch
@@ -266,7 +270,8 @@ class DbsContext:
                                                            dev(case.c_o), dev(case.dv))
         self.cfg = make_config(case.n_d, case.n_o, precision=precision, mode=mode, objective=case.obj_kind,
                                refresh_k=refresh_k, delay_r=delay_r, n_ctas=n_ctas, tau=tau,
-                               obj_weights=case.obj_weights, s_off=case.s_off, s_scale=case.s_scale)
+                               obj_weights=case.obj_weights, s_off=case.s_off, s_scale=case.s_scale,
+                               tensor_fold=tensor_fold)
         self.ws_bytes = pngf_workspace_size(self.cfg)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         self.ctx = pngf_create(self.cfg, self.G.data_ptr(), self.God.data_ptr(), self.cd.data_ptr(),

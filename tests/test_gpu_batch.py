@@ -39,8 +39,9 @@ def _runs(fdfd64):
     return subs, seeds
 
 
-@pytest.mark.parametrize("precision,mode", [("fp64", "first"), ("fp64", "best"), ("mixed", "first")])
-def test_batch_equals_solo_runs(P, precision, mode):
+@pytest.mark.parametrize("precision,mode,tensor_fold", [("fp64", "first", 0), ("fp64", "best", 0),
+                                                        ("mixed", "first", 0), ("mixed", "first", 1)])
+def test_batch_equals_solo_runs(P, precision, mode, tensor_fold):
     fdfd64 = W.get_case("fdfd64")
     subs, seeds = _runs(fdfd64)
     prec = P.PNGF_FP64 if precision == "fp64" else P.PNGF_MIXED
@@ -48,7 +49,8 @@ def test_batch_equals_solo_runs(P, precision, mode):
     n_sweeps = 6 if mode == "first" else 200
     # FP64 without refresh: batch and solo runs do the same FP64 operations per
     # pixel, so they must agree bit for bit (the refresh sums in another order)
-    kw = dict(precision=prec, mode=md, tau=1e-9, refresh_k=0 if precision == "fp64" else 16, delay_r=8)
+    kw = dict(precision=prec, mode=md, tau=1e-9, refresh_k=0 if precision == "fp64" else 16, delay_r=8,
+              tensor_fold=tensor_fold)
     orders = [None, W.shuffled_order(64, n_sweeps, 5) if mode == "first" else None, None, None, None]
     solo = []
     for case, seed, order in zip(subs, seeds, orders):

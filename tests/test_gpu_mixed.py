@@ -100,15 +100,15 @@ def _golden(name):
 
 
 @pytest.mark.parametrize("name", ["fdfd64_first_raster", "fdfd64_first_shuffled", "fdfd64_best"])
-@pytest.mark.parametrize("delay_r,refresh_k", [(4, 8), (16, 32), (64, 0)])
-def test_mixed_dbs_matches_oracle(P, fdfd64, name, delay_r, refresh_k):
+@pytest.mark.parametrize("delay_r,refresh_k,tensor_fold", [(4, 8, 0), (16, 32, 0), (64, 0, 0), (32, 32, 1), (64, 64, 1)])
+def test_mixed_dbs_matches_oracle(P, fdfd64, name, delay_r, refresh_k, tensor_fold):
     g = _golden(name)
     case = fdfd64
     sp = g["spec"]
     assert g["min_abs_margin"] > 1e-6 * abs(g["final_f"])  # decisions far from the score error
     b0 = W.random_design(case.n_d, sp["seed"])
     mode = P.PNGF_BEST_IMPROVEMENT if sp["mode"] == O.BEST_IMPROVEMENT else P.PNGF_FIRST_IMPROVEMENT
-    ctx = _ctx(P, case, mode=mode, tau=g["tau"], delay_r=delay_r, refresh_k=refresh_k)
+    ctx = _ctx(P, case, mode=mode, tau=g["tau"], delay_r=delay_r, refresh_k=refresh_k, tensor_fold=tensor_fold)
     ctx.factor(b0)
     order = None if sp["order"] == "raster" else W.shuffled_order(case.n_d, sp["n_sweeps"], seed=sp["seed"])
     res = ctx.dbs_sweep(sp["n_sweeps"], order=order)
@@ -134,7 +134,8 @@ def test_mixed_restore_replays(P, fdfd64):
     assert np.array_equal(r1["trace_f"], r2["trace_f"])
 
 
-def test_mixed_vs_fp64_full_size(P):
+@pytest.mark.parametrize("tensor_fold", [0, 1])
+def test_mixed_vs_fp64_full_size(P, tensor_fold):
     """N_d = 4096 (the bench workload): the mixed run against the FP64 run and
     the oracle; S-parameters of the final design within 1e-4 relative."""
     case = W.get_case("fdfd256")
@@ -142,7 +143,7 @@ def test_mixed_vs_fp64_full_size(P):
     f64 = P.DbsContext(case, precision=P.PNGF_FP64, refresh_k=64)
     f64.factor(b0)
     r64 = f64.dbs_sweep(10)
-    mix = _ctx(P, case, delay_r=64, refresh_k=64)
+    mix = _ctx(P, case, delay_r=64, refresh_k=64, tensor_fold=tensor_fold)
     mix.factor(b0)
     rmx = mix.dbs_sweep(10)
     k64 = [int(r[2]) for r in r64["trace"]]
@@ -156,3 +157,32 @@ def test_mixed_vs_fp64_full_size(P):
     print(f"mixed final-design S error vs oracle {err:.2e}")
     assert err < 1e-4
     assert n_same >= min(100, len(k64))
+
+
+@pytest.mark.parametrize("name,delay_r,n_acc", [("fdfd64", 32, 40), ("fdfd64", 64, 70), ("fdfd256", 64, 140)])
+def test_tensor_fold_matches_cuda_core_fold(P, name, delay_r, n_acc):
+    """The tcgen05 (3xTF32) fold of the delayed set against the FP32 CUDA-core
+    fold, and both against the oracle, across several folds (ragged tiles on
+    the 100-pixel region)."""
+    case = W.get_case(name)
+    b = W.random_design(case.n_d, 2)
+    ctxs = []
+    for tf in (0, 1):
+        c = _ctx(P, case, delay_r=delay_r, refresh_k=0, tensor_fold=tf)
+        c.factor(b)
+        ctxs.append(c)
+    rng = np.random.default_rng(5)
+    pix = rng.choice(case.n_d, n_acc, replace=False)
+    for k in pix:
+        for c in ctxs:
+            c.accept_flip(int(k))
+        b[k] ^= 1
+    s0, s1 = ctxs[0].state(), ctxs[1].state()
+    for key in ("diag", "e", "T"):
+        assert rel(s1[key], s0[key]) < 2e-6, key
+    o0, _ = ctxs[0].eval_ports()
+    o1, _ = ctxs[1].eval_ports()
+    ev = O.evaluate(O.Problem.from_case(case), b)
+    assert s_rel(case, o1, ev.o) < 1e-4
+    assert s_rel(case, o1, o0) < 1e-5
+    assert ctxs[1].sync() == 0
