@@ -78,9 +78,10 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
   if (a.mode == PNGF_FIRST_IMPROVEMENT && a.order) {
     setup_sweep(0);
     if (!grid_sync(ctl)) failed = true;
+    else if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) status = PNGF_EINVAL;
   }
   const long long max_steps = a.n_sweeps;  // BEST mode: one kept flip per step
-  while (!failed) {
+  while (!failed && status != PNGF_EINVAL) {
     const double f = s_f;
     const double thr = accept_threshold(s_op, f);
     // ---- score own pixels and reduce to this CTA's candidate
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     slot ^= 1;
     ++rd;
     const int k = s_k, pos_k = s_pos;
-    if (k == -2 || *reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) {
+    if (k == -2) {  // invalid visiting-order entry
       status = PNGF_EINVAL;
       break;
     }
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
         if (a.order) {
           setup_sweep(s);
           if (!grid_sync(ctl)) { failed = true; break; }
+          if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
         }
         tick(6);
         continue;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
         if (!grid_sync(ctl)) { failed = true; break; }
         setup_sweep(s);
         if (!grid_sync(ctl)) { failed = true; break; }
+        if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
       }
     }
   }

@@ -65,31 +65,31 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
 
+// Grid barrier on one monotonically increasing arrival counter (reset to 0
+// before every launch): the arrival that returns `old` belongs to barrier
+// old / P, which is complete once the counter reaches (old / P + 1) P.  One
+// atomic per CTA and no generation word, so the last arrival releases the
+// others without a further round trip.  The spin is bounded: on expiry the
+// CTA latches PNGF_ETIMEOUT and returns false.
 __device__ bool grid_sync(Control* ctl) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned g = ld_volatile(&ctl->bar_gen);
     __threadfence();
-    unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      unsigned long long it = 0;
-      while (ld_volatile(&ctl->bar_gen) == g) {
-        if (++it > kSpinLimit) {
-          latch_status(ctl, PNGF_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(128);
+    const unsigned P = gridDim.x;
+    const unsigned old = atomicAdd(&ctl->bar_count, 1u);
+    const unsigned target = (old / P + 1) * P;
+    unsigned long long it = 0;
+    while ((int)(ld_volatile(&ctl->bar_count) - target) < 0) {
+      if (++it > kSpinLimit) {
+        latch_status(ctl, PNGF_ETIMEOUT);
+        ok = 0;
+        break;
       }
+      if (it > 32) __nanosleep(32);
     }
     __threadfence();
-    if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_ETIMEOUT) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

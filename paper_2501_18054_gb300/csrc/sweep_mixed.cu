@@ -106,9 +106,10 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   if (a.mode == PNGF_FIRST_IMPROVEMENT && a.order) {
     setup_sweep(0);
     if (!grid_sync(ctl)) failed = true;
+    else if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) status = PNGF_EINVAL;
   }
   const long long max_steps = a.n_sweeps;
-  while (!failed) {
+  while (!failed && status != PNGF_EINVAL) {
     const double f = s_f;
     const double thr = accept_threshold(s_op, f);
     // ---- score own pixels; the CTA's best candidate and its state go to a record
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           win = (int)(key & 1023u);
           int pos = (int)(key >> 10);
           k_pre = a.order ? a.order[(size_t)s * n + pos] : pos;
+          if ((unsigned)k_pre >= (unsigned)n) win = -2;
           if ((unsigned)k_pre < (unsigned)n) {
             for (int i = lane; i < r; i += 32) {
               c128 al = a.xa[i];
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         if (q_best >= 0 && g - thr > 0.0) win = q_best;
       }
       if (lane == 0) {
-        s_k = -1;
+        s_k = win == -2 ? -2 : -1;
         s_pos = 0;
         if (win >= 0) {
           CandRecord rw = *rec_at(a, slot, win);
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     slot ^= 1;
     ++rd;
     const int k = s_k, pos_k = s_pos;
-    if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) {
+    if (k == -2) {  // invalid visiting-order entry
       status = PNGF_EINVAL;
       break;
     }
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         if (a.order) {
           setup_sweep(s);
           if (!grid_sync(ctl)) { failed = true; break; }
+          if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
         }
         tick(6);
         continue;
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         if (!grid_sync(ctl)) { failed = true; break; }
         setup_sweep(s);
         if (!grid_sync(ctl)) { failed = true; break; }
+        if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
       }
     }
   }

@@ -281,3 +281,19 @@ def test_full_size_fdfd256_sampled(P):
             assert abs(res["trace_f"][i] - f1) < 1e-9 * abs(f1)
         b[k] ^= 1
     assert np.array_equal(b, b_end)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_invalid_order_is_rejected_on_device(P, fdfd64, precision):
+    """An out-of-range visiting-order entry latches PNGF_EINVAL (never used as an index)."""
+    kw = {} if precision == "fp64" else dict(precision=P.PNGF_MIXED, delay_r=8, refresh_k=16)
+    ctx = _ctx(P, fdfd64, **kw)
+    ctx.factor(W.random_design(fdfd64.n_d, 0))
+    order = W.raster_order(fdfd64.n_d, 2)
+    order[1, 17] = fdfd64.n_d + 5  # second sweep holds a bad entry
+    with pytest.raises(P.PngfError) as ei:
+        ctx.dbs_sweep(2, order=order)
+    assert ei.value.status == P.PNGF_EINVAL
+    # the context stays usable: a valid call afterwards succeeds
+    res = ctx.dbs_sweep(1)
+    assert res["counters"][6] in (P.PNGF_OK, P.PNGF_ECAPACITY)
