@@ -93,7 +93,7 @@ typedef struct {
   double tau;         /* accept iff gain > tau * max(|f|, 1e-30) */
   double obj_weights[PNGF_MAX_PORTS]; /* w_p */
   double s_off[2 * PNGF_MAX_PORTS];   /* c128 per port */
-  double s_scale[2 * PNGF_MAX_PORTS]; /* c128 per port */
+  double s_scale[2 * PNGF_MAX_PORTS]; /* c128 per port, nonzero for p < n_o */
   int32_t tensor_fold; /* PNGF_MIXED: 1 = fold the delayed set into the FP32 inverse on the
                           tensor cores (tcgen05, 3xTF32), 0 = FP32 CUDA cores */
   int32_t reserved;
@@ -183,6 +183,9 @@ pngf_status pngf_accept_flip_noalloc(pngf_ctx* ctx, int32_t pixel);
  *             [3] converged (0/1), [4] refreshes, [5] flushes, [6] status, [7] 0
  * Kept flips past trace_cap are still applied but not recorded; [6] is then
  * PNGF_ECAPACITY.  The state stays on the device for further calls.
+ * Mixed precision keeps each CTA's share of the pixels in shared memory:
+ * N_d must not exceed 128 x the persistent grid (one CTA per SM, or n_ctas),
+ * else PNGF_EINVAL before any launch.
  */
 pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order,
                            int32_t* trace, double* trace_f, int32_t trace_cap,
@@ -190,10 +193,10 @@ pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order
 
 /*
  * Batched DBS: many independent runs advanced by one kernel launch, one CTA
- * per run at a time.  Independent systems need no communication (the paper
- * updates its per-frequency systems "in parallel without any communication
- * overhead", section "Computational efficiency"); here they are independent
- * random starts and/or design regions of different sizes sharing one device.
+ * per run at a time.  Independent systems exchange nothing (the paper's
+ * section on computational efficiency advances its per-frequency systems side
+ * by side for that reason); here they are independent random starts and/or
+ * design regions of different sizes sharing one device.
  *   ctxs      host array of n_ctx factored contexts (1 <= n_ctx <= PNGF_BATCH_MAX_RUNS),
  *             one device, one precision and mode, n_d <= PNGF_BATCH_MAX_ND each;
  *             the launch goes to ctxs[0]'s stream, which must order every

@@ -51,7 +51,8 @@ Layout make_layout(const pngf_config& cfg) {
   L.state_bytes = off - L.diag;
   L.pos_of = take(n * sizeof(int));
   L.part = take((size_t)L.n_part * (2 * sizeof(long long) + 2 * sizeof(double) + kMaxPorts * c));
-  L.rec = take((size_t)2 * L.n_part * 256);
+  L.rec = take((size_t)2 * L.n_part * kRecordBytes);
+  L.slots = take((size_t)2 * L.n_part * 128);  // [2][P] one 128-B line per CTA
   if (mixed) {
     const size_t nk = (size_t)(L.R + TC_KC - 1) / TC_KC;
     L.tcimgA_bytes = (size_t)((n + TC_M - 1) / TC_M) * nk * TC_ACHUNK;
@@ -60,6 +61,7 @@ Layout make_layout(const pngf_config& cfg) {
   L.tcimg = take(L.tcimg_bytes);
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
+  L.cpart = take((size_t)ct_tiles((int)n) * 2 * (1 + n_o) * CT * sizeof(float2));  // refresh tile partials
   L.ipiv = take(2 * n * sizeof(int));
   L.snapW = take(L.snapW_bytes);
   L.snapState = take(L.state_bytes + sizeof(Control));
@@ -82,6 +84,8 @@ static pngf_status check_config(const pngf_config* cfg) {
     if (cfg->refresh_k % cfg->delay_r != 0) return PNGF_EINVAL;  // refresh right after a flush
   }
   if (!(cfg->tau >= 0.0)) return PNGF_EINVAL;
+  for (int p = 0; p < cfg->n_o; ++p)  // S_p = (o_p - off_p) scale_p must be invertible
+    if (cfg->s_scale[2 * p] == 0.0 && cfg->s_scale[2 * p + 1] == 0.0) return PNGF_EINVAL;
   return PNGF_OK;
 }
 

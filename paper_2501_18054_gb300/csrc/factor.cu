@@ -1,5 +1,5 @@
 // Initial factorisation of the reduced system and formation of the maintained
-// state (the paper's "inverse of the initial system matrix C_0", section
+// state (the inverse of the paper's initial system matrix C_0, section
 // "Direct binary search optimization"; field form of Supplementary Note 4):
 //
 //   M = I - G diag(v),  v = dv .* b

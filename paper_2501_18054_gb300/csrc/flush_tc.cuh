@@ -115,7 +115,7 @@ __device__ __forceinline__ void tc_tile(long long t, int n, int& ti, int& tj) {
 // Prepare pass (all threads of the calling grid, elements split round-robin):
 // split images of Y = X diag(alpha) (A side, 128-row blocks) and X (B side,
 // 64-row blocks), for nk = ceil(r / 32) chunks, zero-padded past n and r.
-__device__ void tc_prepare(const SweepArgs& a, int r, unsigned char* imgA, unsigned char* imgB, long long gtid,
+__device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char* imgA, unsigned char* imgB, long long gtid,
                            long long gstride) {
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
   const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N - 1) / TC_N;

@@ -8,7 +8,7 @@
 namespace pngf {
 namespace {
 
-static_assert(sizeof(CandRecord) <= 256, "candidate record slot");
+static_assert(sizeof(CandRecord) <= kRecordBytes, "candidate record slot");
 constexpr int kMaxDelay = 128;
 
 __device__ __forceinline__ CandRecord* rec_at(const SweepArgs& a, int slot, int q) {
@@ -164,7 +164,7 @@ __device__ __forceinline__ void flush_tile_fma(const SweepArgs& a, int r, const 
   }
 }
 
-__device__ void flush_tiles(const SweepArgs& a, int r, float* smem, long long t_begin, long long t_step) {
+__device__ __noinline__ void flush_tiles(const SweepArgs& a, int r, float* smem, long long t_begin, long long t_step) {
   const int n = a.n;
   const int tn = (n + FT - 1) / FT;
   const long long n_tiles = (long long)tn * (tn + 1) / 2;

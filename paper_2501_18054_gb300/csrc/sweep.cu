@@ -29,6 +29,7 @@ namespace {
 
 // ---------------------------------------------------------------- persistent DBS
 __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
+  extern __shared__ int act_smem[];  // n entries: active-pixel list of the refresh
   const int P = gridDim.x, cta = blockIdx.x;
   const int n = a.n;
   const int pb = (int)((long long)n * cta / P), pe = (int)((long long)n * (cta + 1) / P);
@@ -228,10 +229,12 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       refresh_x(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(8);
-      refresh_residual(a, pb, pe);
+      refresh_residual(a, pb, pe, act_smem);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(9);
-      refresh_correct(a, pb, pe);
+      correct_tiles(a, reinterpret_cast<float*>(act_smem));
+      if (!grid_sync(ctl)) { failed = true; break; }
+      correct_finish(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(10);
       ports_partial(a, pb, pe);
@@ -345,9 +348,20 @@ __global__ void __launch_bounds__(kThreads) accept_update_kernel(SweepArgs a, co
 
 }  // namespace
 
+// active-pixel list of the refresh residual, then the tile stage of the correction
+static size_t fp64_smem(int n) {
+  const size_t act = (size_t)n * sizeof(int), ct = ct_smem_bytes(1 + kMaxPorts);
+  return act > ct ? act : ct;
+}
+
 int sweep_grid_size(pngf_ctx* c) {
+  static bool attr = false;
+  if (!attr) {  // room for the largest region (n_d <= 32768)
+    cudaFuncSetAttribute(dbs_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem(32768));
+    attr = true;
+  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_fp64_kernel, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_fp64_kernel, kThreads, fp64_smem(c->cfg.n_d));
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;
   int g = c->n_sm * per_sm;
@@ -373,8 +387,8 @@ pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* 
   if (err != cudaSuccess) return PNGF_ECUDA;
   int grid = c->coop_ctas;
   void* params[] = {&a};
-  err = cudaLaunchCooperativeKernel((const void*)dbs_fp64_kernel, dim3(grid), dim3(kThreads), params, 0,
-                                    c->stream);
+  err = cudaLaunchCooperativeKernel((const void*)dbs_fp64_kernel, dim3(grid), dim3(kThreads), params,
+                                    fp64_smem(c->cfg.n_d), c->stream);
   return cuda_status(err);
 }
 

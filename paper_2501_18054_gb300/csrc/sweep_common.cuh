@@ -47,6 +47,8 @@ struct SweepArgs {
   float2* X;  // n x R delayed columns c_i in FP32 (row j holds c_0[j] .. c_{R-1}[j])
   c128* xa;   // R coefficients alpha_i
   void* rec;  // [2][P] candidate records
+  unsigned long long* slots;  // [2][P] round words of the mixed search, 128 B apart
+  float2* cpart;              // tile partial sums of the refresh correction
 };
 
 // a CTA's candidate of one scoring round, with the state the pivot needs
@@ -65,6 +67,12 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
 
+// Acquire/release fence at GPU scope.  Paired with a relaxed store (release)
+// or after a relaxed load (acquire) it orders exactly what the barrier and
+// the word exchange need, and it is lighter than the sequentially consistent
+// fence of __threadfence().
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Grid barrier on one monotonically increasing arrival counter (reset to 0
 // before every launch): the arrival that returns `old` belongs to barrier
 // old / P, which is complete once the counter reaches (old / P + 1) P.  One
@@ -76,7 +84,7 @@ __device__ bool grid_sync(Control* ctl) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
+    fence_acq_rel_gpu();  // release: this CTA's writes before its arrival
     const unsigned P = gridDim.x;
     const unsigned old = atomicAdd(&ctl->bar_count, 1u);
     const unsigned target = (old / P + 1) * P;
@@ -89,7 +97,7 @@ __device__ bool grid_sync(Control* ctl) {
       }
       if (it > 32) __nanosleep(32);
     }
-    __threadfence();
+    fence_acq_rel_gpu();  // acquire: every CTA's writes before the others' arrivals
     s_ok = ok;
   }
   __syncthreads();
@@ -331,20 +339,69 @@ __device__ void refresh_x(const SweepArgs& a, int pb, int pe) {
 // template parameter: every loop over the vectors is then fully unrolled with
 // no predicated-off FP64 work (the FP64 pipe is the scarce one on GB300).
 
-// R1: residuals of own rows (row j of G dotted with x), and x2 = v.r
-template <int NV>
-__device__ __noinline__ void refresh_residual_t(const SweepArgs& a, int pb, int pe) {
+// Ascending list of the pixels with b_i = 1 (the only nonzero entries of
+// x = v.[e, T]) in shared memory act[0, m); returns m (the same in every thread).
+__device__ int active_list(const SweepArgs& a, int* act) {
+  __shared__ int s_scan[kThreads / 32];
+  __shared__ int s_m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int chunk = (a.n + blockDim.x - 1) / blockDim.x;
+  const int i0 = min(a.n, (int)threadIdx.x * chunk), i1 = min(a.n, i0 + chunk);
+  int c = 0;
+  for (int i = i0; i < i1; ++i) c += a.b[i] != 0;
+  int incl = c;  // inclusive scan over the block, thread order = pixel order
+  for (int off = 1; off < 32; off <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) s_scan[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? s_scan[lane] : 0;
+    for (int off = 1; off < 32; off <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < nw) s_scan[lane] = w;
+    if (lane == nw - 1) s_m = w;
+  }
+  __syncthreads();
+  int o = incl - c + (warp > 0 ? s_scan[warp - 1] : 0);
+  for (int i = i0; i < i1; ++i)
+    if (a.b[i]) act[o++] = i;
+  __syncthreads();
+  return s_m;
+}
+
+// R1: residuals of own rows (row j of G dotted with x), and x2 = v.r.  With
+// act (shared memory, room for n entries) only the columns of G at pixels
+// with b_i = 1 are visited: x vanishes elsewhere, so the FP64 work follows the
+// number of "on" pixels instead of n.
+template <int NV>
+__device__ __noinline__ int refresh_residual_t(const SweepArgs& a, int pb, int pe, int* act) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = act ? active_list(a, act) : a.n;
   for (int j = pb + warp; j < pe; j += nw) {
     const c128* g = a.G + (size_t)j * a.n;
     c128 acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = mk(0.0, 0.0);
+    if (act) {
 #pragma unroll 4
-    for (int i = lane; i < a.n; i += 32) {
-      c128 gi = g[i];
+      for (int t = lane; t < m; t += 32) {
+        const int i = act[t];
+        c128 gi = g[i];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
+        for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
+      }
+    } else {
+#pragma unroll 4
+      for (int i = lane; i < a.n; i += 32) {
+        c128 gi = g[i];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
+      }
     }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -359,6 +416,7 @@ __device__ __noinline__ void refresh_residual_t(const SweepArgs& a, int pb, int 
       }
     }
   }
+  return m;
 }
 
 // R2: corrections (I + W V) r for own rows, W symmetric with its upper
@@ -392,22 +450,50 @@ __device__ __forceinline__ f2c w_upper(const SweepArgs& a, int i, int j) {
   return f2(a.W[(size_t)i * a.ldw + j]);
 }
 
+// four consecutive elements W(j, i0 .. i0+3) of the maintained W as FP32
+// (i0 % 4 == 0; rows are padded to a multiple of 4 so the read stays inside
+// the row; elements past n are masked by the caller)
+__device__ __forceinline__ void w_row4(const SweepArgs& a, int j, int i0, f2c w[4]) {
+  if (a.mixed) {
+    const size_t o = (size_t)j * a.ldl + i0;
+    const float4 re = *reinterpret_cast<const float4*>(a.Wr + o);
+    const float4 im = *reinterpret_cast<const float4*>(a.Wi + o);
+    w[0] = f2c{re.x, im.x};
+    w[1] = f2c{re.y, im.y};
+    w[2] = f2c{re.z, im.z};
+    w[3] = f2c{re.w, im.w};
+  } else {
+    const c128* p = a.W + (size_t)j * a.ldw + i0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = f2(p[u]);
+  }
+}
+
+// R2, upper part: one warp per own row j, sum over i >= j of W[j][i] x2_i
+// with four-wide row reads, four chunks in flight per lane.
 template <int NV>
-__device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int pe) {
-  __shared__ f2c red[kThreads / 32][32];
+__device__ __forceinline__ void correct_upper(const SweepArgs& a, int pb, int pe) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // upper part, one warp per own row
+  const int n = a.n;
   for (int j = pb + warp; j < pe; j += nw) {
     f2c acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
+    const int ib = j & ~3;
 #pragma unroll 4
-    for (int i = j + lane; i < a.n; i += 32) {
-      f2c wi = w_upper(a, j, i);
+    for (int i0 = ib + 4 * lane; i0 < n; i0 += 128) {
+      f2c w[4];
+      w_row4(a, j, i0, w);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        float2 x = x2f(a, q)[i];
-        acc[q] = f2fma(wi, f2c{x.x, x.y}, acc[q]);
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        if (i >= j && i < n) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const float2 x = x2f(a, q)[i];
+            acc[q] = f2fma(w[u], f2c{x.x, x.y}, acc[q]);
+          }
+        }
       }
     }
 #pragma unroll
@@ -416,22 +502,61 @@ __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int p
       if (lane == 0) rvec(a, 3, q)[j] = mk(sum.x, sum.y);
     }
   }
+}
+
+// R2: corrections (I + W V) r for own rows, W symmetric with its upper
+// triangle current: row j takes sum_{i>=j} W[j][i] x2_i from its own row and
+// sum_{i<j} W[i][j] x2_i from the rows above (a strip of columns [pb, pe)).
+// The residual r is FP64; the product W x2 only has to be accurate relative
+// to |r| (classic mixed-precision iterative refinement), so it runs in FP32
+// arithmetic and is added to r in FP64.  x2 = v.r vanishes where b_i = 0, so
+// with the active list act[0, m) only those rows of the strip are read.
+template <int NV>
+__device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int pe, const int* act, int m) {
+  __shared__ f2c red[kThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  correct_upper<NV>(a, pb, pe);
   __syncthreads();
-  // lower part: columns of this CTA in chunks of 32, rows above spread over warps
+  // lower part: columns of this CTA in blocks of 32 (lane = column), the rows
+  // above spread over the warps, eight rows in flight per warp
+  int t_end;  // rows i < pe - 1 only (the active list is ascending)
+  if (act) {
+    int lo = 0, hi = m;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (act[mid] < pe - 1) lo = mid + 1; else hi = mid;
+    }
+    t_end = lo;
+  } else {
+    t_end = max(pe - 1, 0);
+  }
   for (int c0 = pb; c0 < pe; c0 += 32) {
     const int j = c0 + lane;
-    const int rows = min(pe, c0 + 32) - 1;  // rows i < j <= rows
+    const bool colok = j < pe;
     f2c acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
-#pragma unroll 4
-    for (int i = warp; i < rows; i += nw) {
-      if (i < j && j < pe) {
-        f2c wij = w_upper(a, i, j);
+    for (int t = warp; t < t_end; t += 8 * nw) {
+      int ii[8];
+      f2c w[8];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          float2 x = x2f(a, q)[i];
-          acc[q] = f2fma(wij, f2c{x.x, x.y}, acc[q]);
+      for (int u = 0; u < 8; ++u) {
+        const int tu = t + u * nw;
+        ii[u] = tu < t_end ? (act ? act[tu] : tu) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        w[u] = f2c{0.f, 0.f};
+        if (ii[u] >= 0 && colok && ii[u] < j) w[u] = w_upper(a, ii[u], j);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (ii[u] >= 0 && colok && ii[u] < j) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const float2 x = x2f(a, q)[ii[u]];
+            acc[q] = f2fma(w[u], f2c{x.x, x.y}, acc[q]);
+          }
         }
       }
     }
@@ -439,7 +564,7 @@ __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int p
     for (int q = 0; q < NV; ++q) {
       red[warp][lane] = acc[q];
       __syncthreads();
-      if (warp == 0 && j < pe) {
+      if (warp == 0 && colok) {
         double lx = 0.0, ly = 0.0;
         for (int w2 = 0; w2 < nw; ++w2) {
           lx += red[w2][lane].x;
@@ -449,8 +574,8 @@ __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int p
         if (q == 0) {
           a.e[j] = cadd(a.e[j], d);
         } else {
-          c128* t = a.T + (size_t)(q - 1) * a.ldt + j;
-          *t = cadd(*t, d);
+          c128* tq = a.T + (size_t)(q - 1) * a.ldt + j;
+          *tq = cadd(*tq, d);
         }
       }
       __syncthreads();
@@ -458,29 +583,220 @@ __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int p
   }
 }
 
-__device__ void refresh_residual(const SweepArgs& a, int pb, int pe) {
+// act: shared memory for n pixel indices, or nullptr (dense visit of all
+// columns); returns the length of the active list (n when dense)
+__device__ int refresh_residual(const SweepArgs& a, int pb, int pe, int* act = nullptr) {
   switch (a.n_o) {
-    case 1: refresh_residual_t<2>(a, pb, pe); break;
-    case 2: refresh_residual_t<3>(a, pb, pe); break;
-    case 3: refresh_residual_t<4>(a, pb, pe); break;
-    case 4: refresh_residual_t<5>(a, pb, pe); break;
-    case 5: refresh_residual_t<6>(a, pb, pe); break;
-    case 6: refresh_residual_t<7>(a, pb, pe); break;
-    case 7: refresh_residual_t<8>(a, pb, pe); break;
-    default: refresh_residual_t<9>(a, pb, pe); break;
+    case 1: return refresh_residual_t<2>(a, pb, pe, act);
+    case 2: return refresh_residual_t<3>(a, pb, pe, act);
+    case 3: return refresh_residual_t<4>(a, pb, pe, act);
+    case 4: return refresh_residual_t<5>(a, pb, pe, act);
+    case 5: return refresh_residual_t<6>(a, pb, pe, act);
+    case 6: return refresh_residual_t<7>(a, pb, pe, act);
+    case 7: return refresh_residual_t<8>(a, pb, pe, act);
+    default: return refresh_residual_t<9>(a, pb, pe, act);
   }
 }
 
-__device__ void refresh_correct(const SweepArgs& a, int pb, int pe) {
+// act, m: the active list left by refresh_residual in this CTA, or nullptr
+__device__ void refresh_correct(const SweepArgs& a, int pb, int pe, const int* act = nullptr, int m = 0) {
   switch (a.n_o) {
-    case 1: refresh_correct_t<2>(a, pb, pe); break;
-    case 2: refresh_correct_t<3>(a, pb, pe); break;
-    case 3: refresh_correct_t<4>(a, pb, pe); break;
-    case 4: refresh_correct_t<5>(a, pb, pe); break;
-    case 5: refresh_correct_t<6>(a, pb, pe); break;
-    case 6: refresh_correct_t<7>(a, pb, pe); break;
-    case 7: refresh_correct_t<8>(a, pb, pe); break;
-    default: refresh_correct_t<9>(a, pb, pe); break;
+    case 1: refresh_correct_t<2>(a, pb, pe, act, m); break;
+    case 2: refresh_correct_t<3>(a, pb, pe, act, m); break;
+    case 3: refresh_correct_t<4>(a, pb, pe, act, m); break;
+    case 4: refresh_correct_t<5>(a, pb, pe, act, m); break;
+    case 5: refresh_correct_t<6>(a, pb, pe, act, m); break;
+    case 6: refresh_correct_t<7>(a, pb, pe, act, m); break;
+    case 7: refresh_correct_t<8>(a, pb, pe, act, m); break;
+    default: refresh_correct_t<9>(a, pb, pe, act, m); break;
+  }
+}
+
+// ---------------------------------------------------------------- refresh correction, tiled
+// The persistent kernels form y = W x2 (x2 = v.r, W symmetric with its upper
+// triangle current) by 64 x 64 tiles of the upper triangle: a tile (I, J),
+// I <= J, is read once and yields both its row sums W[I, J] x2[J] (for block
+// I) and its column sums W[I, J]^T x2[I] (for block J); on a diagonal tile the
+// row sums take the upper part including the diagonal and the column sums
+// the strict upper part.  Partial sums go to cpart, tile by tile, and the
+// owner of a row adds them in a fixed order (deterministic, no atomics).
+constexpr int CT = 64;
+
+__host__ __device__ __forceinline__ long long ct_tiles(int n) {
+  const long long tn = (n + CT - 1) / CT;
+  return tn * (tn + 1) / 2;
+}
+__device__ __forceinline__ long long ct_index(int I, int J, int tn) {
+  return (long long)I * tn - (long long)I * (I - 1) / 2 + (J - I);
+}
+// cpart[((t * 2 + side) * NV + q) * CT + i], side 0: row sums, 1: column sums
+__device__ __forceinline__ float2* ct_part(const SweepArgs& a, long long t, int side, int q, int nv) {
+  return a.cpart + (((size_t)t * 2 + side) * nv + q) * CT;
+}
+// shared memory of correct_tiles_t: x2 of both blocks and one column-sum stage
+__host__ __device__ constexpr size_t ct_smem_bytes(int nv) {
+  return (size_t)2 * nv * CT * sizeof(float2) + (size_t)(kThreads / 32) * CT * sizeof(float2);
+}
+
+template <int NV>
+__device__ __noinline__ void correct_tiles_t(const SweepArgs& a, float* smem) {
+  const int n = a.n, tn = (n + CT - 1) / CT;
+  const long long T = ct_tiles(n);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = tid & 15, ty = tid >> 4;  // columns 4 tx .. 4 tx + 3, rows 2 ty, 2 ty + 1
+  float2* xJ = reinterpret_cast<float2*>(smem);  // [NV][CT]
+  float2* xI = xJ + NV * CT;                     // [NV][CT]
+  float2* cst = xI + NV * CT;                    // [warps][CT]
+  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
+    int I, J;
+    tri_rc(t, tn, I, J);
+    const int i0 = I * CT, j0 = J * CT;
+    const bool diag = I == J;
+    __syncthreads();
+    for (int q = tid; q < NV * CT; q += blockDim.x) {
+      const int v = q / CT, c = q - v * CT;
+      xJ[q] = j0 + c < n ? x2f(a, v)[j0 + c] : make_float2(0.f, 0.f);
+      xI[q] = i0 + c < n ? x2f(a, v)[i0 + c] : make_float2(0.f, 0.f);
+    }
+    // the tile in registers (masked entries are zero)
+    f2c w[2][4];
+    const int cg = j0 + 4 * tx;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int rg = i0 + 2 * ty + u;
+      if (rg < n && cg < n) {
+        w_row4(a, rg, cg, w[u]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[u][c] = f2c{0.f, 0.f};
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (cg + c >= n || (diag && cg + c < rg)) w[u][c] = f2c{0.f, 0.f};  // upper part only
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int q = 0; q < NV; ++q) {
+      // row sums over this thread's four columns, then over the 16 column groups
+      f2c rs[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        rs[u] = f2c{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 x = xJ[q * CT + 4 * tx + c];
+          rs[u] = f2fma(w[u][c], f2c{x.x, x.y}, rs[u]);
+        }
+#pragma unroll
+        for (int off = 1; off < 16; off <<= 1) {
+          rs[u].x += __shfl_xor_sync(0xffffffffu, rs[u].x, off);
+          rs[u].y += __shfl_xor_sync(0xffffffffu, rs[u].y, off);
+        }
+      }
+      if (tx == 0) {
+        float2* pr = ct_part(a, t, 0, q, NV);
+        pr[2 * ty] = make_float2(rs[0].x, rs[0].y);
+        pr[2 * ty + 1] = make_float2(rs[1].x, rs[1].y);
+      }
+      // column sums over this thread's two rows (strict upper part on a diagonal tile)
+      f2c cs[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        cs[c] = f2c{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (diag && cg + c == i0 + 2 * ty + u) continue;  // the diagonal belongs to the row sums
+          const float2 x = xI[q * CT + 2 * ty + u];
+          cs[c] = f2fma(w[u][c], f2c{x.x, x.y}, cs[c]);
+        }
+        cs[c].x += __shfl_xor_sync(0xffffffffu, cs[c].x, 16);
+        cs[c].y += __shfl_xor_sync(0xffffffffu, cs[c].y, 16);
+      }
+      if (lane < 16)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cst[warp * CT + 4 * tx + c] = make_float2(cs[c].x, cs[c].y);
+      __syncthreads();
+      if (tid < CT) {
+        float sx = 0.f, sy = 0.f;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+          sx += cst[w2 * CT + tid].x;
+          sy += cst[w2 * CT + tid].y;
+        }
+        ct_part(a, t, 1, q, NV)[tid] = make_float2(sx, sy);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// after a grid barrier: e, T of own rows += r + y, y summed from the tile
+// partials in a fixed order (one warp per row, lanes over the tiles)
+template <int NV>
+__device__ __noinline__ void correct_finish_t(const SweepArgs& a, int pb, int pe) {
+  const int n = a.n, tn = (n + CT - 1) / CT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = pb + warp; j < pe; j += nw) {
+    const int B = j / CT, rho = j - B * CT;
+    const int nterm = tn + 1;  // row sums of tiles (B, J >= B), column sums of tiles (I <= B, B)
+    float sx[NV], sy[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sx[q] = sy[q] = 0.f;
+#pragma unroll 4
+    for (int u = lane; u < nterm; u += 32) {
+      const float2* base = u < tn - B ? ct_part(a, ct_index(B, B + u, tn), 0, 0, NV)
+                                      : ct_part(a, ct_index(u - (tn - B), B, tn), 1, 0, NV);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float2 p = base[q * CT + rho];
+        sx[q] += p.x;
+        sy[q] += p.y;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      for (int off = 16; off > 0; off >>= 1) {
+        sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], off);
+        sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], off);
+      }
+    }
+    if (lane < NV) {  // lane q updates vector q (e for q = 0, row q - 1 of T otherwise)
+      float fx = 0.f, fy = 0.f;
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        if (q == lane) {
+          fx = sx[q];
+          fy = sy[q];
+        }
+      const c128 d = cadd(rvec(a, 0, lane)[j], mk((double)fx, (double)fy));
+      c128* dst = lane == 0 ? a.e + j : a.T + (size_t)(lane - 1) * a.ldt + j;
+      *dst = cadd(*dst, d);
+    }
+  }
+}
+
+__device__ void correct_tiles(const SweepArgs& a, float* smem) {
+  switch (a.n_o) {
+    case 1: correct_tiles_t<2>(a, smem); break;
+    case 2: correct_tiles_t<3>(a, smem); break;
+    case 3: correct_tiles_t<4>(a, smem); break;
+    case 4: correct_tiles_t<5>(a, smem); break;
+    case 5: correct_tiles_t<6>(a, smem); break;
+    case 6: correct_tiles_t<7>(a, smem); break;
+    case 7: correct_tiles_t<8>(a, smem); break;
+    default: correct_tiles_t<9>(a, smem); break;
+  }
+}
+
+__device__ void correct_finish(const SweepArgs& a, int pb, int pe) {
+  switch (a.n_o) {
+    case 1: correct_finish_t<2>(a, pb, pe); break;
+    case 2: correct_finish_t<3>(a, pb, pe); break;
+    case 3: correct_finish_t<4>(a, pb, pe); break;
+    case 4: correct_finish_t<5>(a, pb, pe); break;
+    case 5: correct_finish_t<6>(a, pb, pe); break;
+    case 6: correct_finish_t<7>(a, pb, pe); break;
+    case 7: correct_finish_t<8>(a, pb, pe); break;
+    default: correct_finish_t<9>(a, pb, pe); break;
   }
 }
 
@@ -542,6 +858,8 @@ SweepArgs make_args(pngf_ctx* c) {
   a.X = at<float2>(c, L.X);
   a.xa = at<c128>(c, L.xa);
   a.rec = c->ws + L.rec;
+  a.slots = at<unsigned long long>(c, L.slots);
+  a.cpart = at<float2>(c, L.cpart);
   a.tensor_fold = c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold;
   a.tcimgA = reinterpret_cast<unsigned char*>(c->ws) + L.tcimg;
   a.tcimgB = a.tcimgA + L.tcimgA_bytes;

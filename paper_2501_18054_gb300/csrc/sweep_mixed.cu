@@ -16,8 +16,8 @@
 // and T are refined in FP64 against G.
 //
 // Each CTA publishes its best candidate together with the pixel state the
-// pivot needs, so one grid barrier per kept flip suffices: nobody reads the
-// state arrays of the chosen pixel while its owner updates them.
+// pivot needs, and the CTAs agree on the kept flip by exchanging one word
+// each: no grid barrier per kept flip, only around the fold and the refresh.
 #include <cstdio>
 
 #include "flush_tc.cuh"
@@ -26,32 +26,167 @@ namespace pngf {
 namespace {
 
 // ---------------------------------------------------------------- persistent mixed DBS
+// Per kept flip the CTAs exchange one 64-bit word each instead of meeting at a
+// grid barrier: word = round sequence number << 44 | candidate key, with key =
+// position << 22 | pixel (FIRST mode) or pixel (BEST mode, gain in the
+// record); every CTA waits for all P words of the round, reduces them itself
+// and fetches the winner's record, the winner's delayed row X[k] and
+// W_lo(k, own) in one parallel round trip.  Words and records alternate
+// between two buffers by round parity: a CTA can run at most one round ahead
+// of the slowest reader, so the buffer it writes is never one still being read.
+//
+// The state of a CTA's own pixels (diag W, e, T, b, visiting position and the
+// delayed rows X[own]) lives in shared memory between refreshes; only b and v
+// of the flipped pixel and the appended column of X are written through.
+//
+// FP64 on GB300 retires one warp instruction per 64 cycles on each SM
+// sub-partition whatever the number of active lanes, so the per-flip FP64
+// chain is kept short: the score needs one real division,
+//   alpha_j = 1 / z_j,  z_j = 1/delta_j - W_jj   (= delta_j / d_j, Eq. 14),
+// with 1/delta_j = -+1/dv_j tabulated, the rows of T are kept pre-multiplied by
+// the port scales so that S_p(new) = S_p + coef T'_p,j is one complex FMA,
+// the winner's record carries f(new) (every CTA forms S(new) with the same
+// operations the scorer used, off the critical path), and the FP64 state
+// update spreads diag, e and the rows of T over warps of different
+// sub-partitions.
+constexpr int kOwnMax = 128;                                       // pixels per CTA
+constexpr int kSlotStride = 16;                                    // 64-bit words between two CTAs' words
+constexpr int kSeqShift = 44;
+constexpr int kPixBits = 22;
+constexpr unsigned long long kKeyMask = (1ull << kSeqShift) - 1;
+constexpr long long kNoCand = (long long)kKeyMask;                 // above every real key
+constexpr unsigned kSeqMask = (1u << (64 - kSeqShift)) - 1;
+// FP64 own state at the start of the dynamic shared memory: T'[kMaxPorts], diag, e, dv, 1/dv, |dv|^2
+constexpr size_t kOwnStateSmem = (size_t)(kMaxPorts + 4) * kOwnMax * sizeof(c128) + kOwnMax * sizeof(double);
+static_assert(kOwnStateSmem % 1024 == 0, "fold operands stay 1024-B aligned");
+
+// a CTA's candidate of one round, with everything the other CTAs need to keep it
+struct MixRecord {
+  long long key;  // FIRST: visiting position
+  double gain;    // BEST: gain of the candidate
+  double f_new;   // objective after the flip
+  int pixel;
+  int b;
+  c128 alpha, coef;
+  c128 dv;
+  c128 Tk[kMaxPorts];  // scaled rows T'_p at the pixel
+};
+static_assert(sizeof(MixRecord) <= kRecordBytes, "record slot");
+
+__device__ __forceinline__ MixRecord* mrec_at(const SweepArgs& a, int par, int q) {
+  return reinterpret_cast<MixRecord*>(a.rec) + (size_t)par * gridDim.x + q;
+}
+
+__device__ __forceinline__ int owner_of(int k, int n, int P) { return (int)(((long long)(k + 1) * P - 1) / n); }
+
+// objective of scaled amplitudes S (w_p |S_p|^2 summed, or w_p (1 - |S_p|)^2 summed)
+__device__ __forceinline__ double objective_term_a2(const ObjParams& op, int p, double a2) {
+  if (op.kind == PNGF_OBJ_MAX_WEIGHTED_POWER) return op.w[p] * a2;
+  double m = 1.0 - sqrt(a2);
+  return op.w[p] * (m * m);
+}
+
+// waits (bounded) for CTA q's word of round `seq`; returns its key
+__device__ __forceinline__ long long poll_word(const unsigned long long* w, unsigned seq, bool& ok) {
+  unsigned long long it = 0;
+  for (;;) {
+    unsigned long long v = *reinterpret_cast<const volatile unsigned long long*>(w);
+    if ((unsigned)(v >> kSeqShift) == seq) return (long long)(v & kKeyMask);
+    if (++it > kSpinLimit) {
+      ok = false;
+      return kNoCand;
+    }
+    if (it > 64) __nanosleep(32);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   extern __shared__ float dyn_smem[];
-  const int P = gridDim.x, cta = blockIdx.x;
-  const int n = a.n;
+  const int P = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n = a.n, n_o = a.n_o;
   const int pb = (int)((long long)n * cta / P), pe = (int)((long long)n * (cta + 1) / P);
+  const int own = pe - pb;
   Control* ctl = a.ctl;
-  __shared__ c128 s_o[kMaxPorts];
+  // own-pixel state (thread jl < own scores pixel pb + jl)
+  c128* s_T = reinterpret_cast<c128*>(dyn_smem);  // [kMaxPorts][kOwnMax], T'_p,j = T_p,j scale_p
+  c128* s_diag = s_T + kMaxPorts * kOwnMax;
+  c128* s_e = s_diag + kOwnMax;
+  c128* s_dv = s_e + kOwnMax;
+  c128* s_idv = s_dv + kOwnMax;                                    // 1 / dv (0 where dv = 0)
+  double* s_dv2 = reinterpret_cast<double*>(s_idv + kOwnMax);      // |dv|^2
+  unsigned char* work = reinterpret_cast<unsigned char*>(dyn_smem) + kOwnStateSmem;
+  __shared__ int s_pos[kOwnMax];
+  __shared__ unsigned char s_b[kOwnMax];
+  __shared__ float2 s_wk[kOwnMax], s_sum[kOwnMax];
+  __shared__ float2 s_beta[kMaxDelay], s_alpha[kMaxDelay];
+  __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
+  __shared__ c128 s_iscale[kMaxPorts];  // 1 / scale_p
   __shared__ double s_f;
   __shared__ Pivot s_pv;
-  __shared__ int s_k, s_pos;
   __shared__ ObjParams s_op;
-  __shared__ float2 s_beta[kMaxDelay];
-  if (threadIdx.x == 0) {
+  __shared__ int s_fail;
+  float2* Xs = reinterpret_cast<float2*>(work);  // [own][R] delayed rows, between folds
+  const int R = a.R;
+  int r = ctl->r_delay;
+  if (tid == 0) {
     s_op = a.op;
-    FOR_PORTS(p, a.n_o) s_o[p] = ctl->o[p];
+    FOR_PORTS(p, n_o) {
+      s_iscale[p] = cdiv(mk(1.0, 0.0), a.op.scale[p]);
+      s_S[p] = cmul(csub(ctl->o[p], a.op.off[p]), a.op.scale[p]);
+    }
     s_f = ctl->f;
+    s_fail = 0;
+  }
+  for (int jl = tid; jl < own; jl += blockDim.x) {
+    const int j = pb + jl;
+    const c128 dv = a.dv[j];
+    s_diag[jl] = a.diag[j];
+    s_e[jl] = a.e[j];
+    s_dv[jl] = dv;
+    s_dv2[jl] = cabs2(dv);
+    s_idv[jl] = cabs2(dv) > 0.0 ? cdiv(mk(1.0, 0.0), dv) : mk(0.0, 0.0);
+    s_b[jl] = a.b[j];
+    for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cmul(a.T[(size_t)p * a.ldt + j], a.op.scale[p]);
+    if (!a.order) s_pos[jl] = j;
+  }
+  for (int q = tid; q < own * r; q += blockDim.x) {
+    const int jl = q / r, i = q - jl * r;
+    Xs[jl * R + i] = a.X[(size_t)(pb + jl) * R + i];
+  }
+  for (int i = tid; i < r; i += blockDim.x) {
+    c128 al = a.xa[i];
+    s_alpha[i] = make_float2((float)al.x, (float)al.y);
   }
   __syncthreads();
+  auto store_et = [&](bool with_diag) {
+    for (int jl = tid; jl < own; jl += blockDim.x) {
+      const int j = pb + jl;
+      a.e[j] = s_e[jl];
+      if (with_diag) a.diag[j] = s_diag[jl];
+      for (int p = 0; p < n_o; ++p) a.T[(size_t)p * a.ldt + j] = cmul(s_T[p * kOwnMax + jl], s_iscale[p]);
+    }
+  };
+  auto load_et = [&]() {
+    for (int jl = tid; jl < own; jl += blockDim.x) {
+      const int j = pb + jl;
+      s_e[jl] = a.e[j];
+      for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cmul(a.T[(size_t)p * a.ldt + j], s_op.scale[p]);
+    }
+  };
+  auto load_pos = [&]() {
+    for (int jl = tid; jl < own; jl += blockDim.x) s_pos[jl] = a.pos_of[pb + jl];
+  };
   long long n_acc = 0, n_evals = 0, n_refresh = 0, n_flush = 0;
   int sweeps_done = 0, converged = 0, status = PNGF_OK;
   int since_refresh = ctl->since_refresh;
-  int r = ctl->r_delay;
-  int s = 0, t = 0, acc_in_sweep = 0, slot = 0, rd = 0;
+  int s = 0, t = 0, acc_in_sweep = 0;
+  long long round = 0;
   bool failed = false;
-  const bool timer = (cta == 0 && threadIdx.x == 0);
-  long long ph[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const bool timer = (cta == 0 && tid == 0);
+  __shared__ long long ph[16];  // phase cycles, kept by the timer thread only
+  if (timer)
+    for (int q = 0; q < 16; ++q) ph[q] = 0;
   long long t_last = clock64(), t_begin = t_last;
   auto tick = [&](int phase) {
     if (timer) {
@@ -60,13 +195,18 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       t_last = now;
     }
   };
-  auto setup_sweep = [&](int sw) {
-    if (a.order)
-      for (int q = pb + threadIdx.x; q < pe; q += blockDim.x) {
-        int px = a.order[(size_t)sw * n + q];
-        if ((unsigned)px < (unsigned)n) a.pos_of[px] = q;
-        else latch_status(ctl, PNGF_EINVAL);
-      }
+  // writes the positions of sweep sw for the visiting positions [pb, pe);
+  // every CTA then reads its own pixels' positions after a barrier
+  auto setup_sweep = [&](int sw) -> bool {
+    for (int q = pb + tid; q < pe; q += blockDim.x) {
+      int px = a.order[(size_t)sw * n + q];
+      if ((unsigned)px < (unsigned)n) a.pos_of[px] = q;
+      else latch_status(ctl, PNGF_EINVAL);
+    }
+    if (!grid_sync(ctl)) return false;
+    if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) status = PNGF_EINVAL;
+    load_pos();
+    return true;
   };
   // tensor-core fold: warp 0 holds TC_TMEM_COLS columns of tensor memory for the whole search
   __shared__ __align__(8) unsigned long long s_mb_load, s_mb_mma;
@@ -84,19 +224,20 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     tcs.mb_load = (unsigned)__cvta_generic_to_shared(&s_mb_load);
     tcs.mb_mma = (unsigned)__cvta_generic_to_shared(&s_mb_mma);
   }
+  // the fold reuses the shared memory of the delayed rows: they are in global
+  // X as well and the delayed set is empty afterwards
   auto flush = [&]() -> bool {
     if (!grid_sync(ctl)) return false;
     if (a.tensor_fold) {
       tc_prepare(a, r, a.tcimgA, a.tcimgB, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                  (long long)gridDim.x * blockDim.x);
       if (!grid_sync(ctl)) return false;
-      if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, reinterpret_cast<unsigned char*>(dyn_smem), tcs, blockIdx.x,
-                         gridDim.x)) {
+      if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, work, tcs, blockIdx.x, gridDim.x)) {
         if (threadIdx.x == 0) latch_status(ctl, PNGF_ETIMEOUT);
         return false;
       }
     } else {
-      flush_tiles(a, r, dyn_smem, blockIdx.x, gridDim.x);
+      flush_tiles(a, r, reinterpret_cast<float*>(work), blockIdx.x, gridDim.x);
     }
     if (!grid_sync(ctl)) return false;
     r = 0;
@@ -104,138 +245,116 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     return true;
   };
   if (a.mode == PNGF_FIRST_IMPROVEMENT && a.order) {
-    setup_sweep(0);
-    if (!grid_sync(ctl)) failed = true;
-    else if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) status = PNGF_EINVAL;
+    if (!setup_sweep(0)) failed = true;
+    __syncthreads();
   }
   const long long max_steps = a.n_sweeps;
   while (!failed && status != PNGF_EINVAL) {
     const double f = s_f;
     const double thr = accept_threshold(s_op, f);
-    // ---- score own pixels; the CTA's best candidate and its state go to a record
+    const int par = (int)(round & 1);
+    const unsigned seq = (unsigned)((round + 1) & kSeqMask);
+    unsigned long long* words = a.slots + (size_t)par * P * kSlotStride;
+    // ---- score own pixels; the CTA's best candidate goes to its record, its key to its word
+    long long key = kNoCand;
     {
-      long long best = LLONG_MAX;
-      double g = -INFINITY;
-      int pix = INT_MAX;
-      c128 b_alpha = mk(0.0, 0.0), b_coef = b_alpha;
-      for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
-        double fn;
-        c128 al, co;
-        if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-          int pos = a.order ? a.pos_of[j] : j;
-          if (pos < t) continue;
-          if (!score_pixel(a, s_op, j, s_o, fn, nullptr, &al, &co)) continue;
-          if (gain_of(s_op, fn, f) - thr > 0.0 && pos < best) {
-            best = pos;
-            pix = j;
-            b_alpha = al;
-            b_coef = co;
-          }
-        } else {
-          if (!score_pixel(a, s_op, j, s_o, fn, nullptr, &al, &co)) continue;
-          double gg = gain_of(s_op, fn, f);
-          if (better(gg, j, g, pix)) {
-            g = gg;
-            pix = j;
-            b_alpha = al;
-            b_coef = co;
-          }
+      double fn = 0.0;
+      c128 al = mk(0.0, 0.0), co = al;
+      bool ok = false;
+      if (tid < own) {
+        const c128 idv = s_idv[tid], w = s_diag[tid];
+        const c128 z = s_b[tid] ? mk(-idv.x - w.x, -idv.y - w.y) : mk(idv.x - w.x, idv.y - w.y);
+        const double z2 = cabs2(z);
+        if (!(z2 * s_dv2[tid] < 1e-28)) {  // |d_j| = |delta_j| |z_j|; singular candidates are skipped
+          const double iz = 1.0 / z2;
+          al = mk(z.x * iz, -z.y * iz);
+          co = cmul(al, s_e[tid]);
+#pragma unroll 1
+          for (int p = 0; p < n_o; ++p)
+            fn += objective_term_a2(s_op, p, cabs2(cfma(co, s_T[p * kOwnMax + tid], s_S[p])));
+          ok = true;
         }
       }
-      CandRecord* rc = rec_at(a, slot, cta);
+      MixRecord* rc = mrec_at(a, par, cta);
+      auto fill = [&](long long kk, double gg) {
+        rc->key = kk;
+        rc->gain = gg;
+        rc->f_new = fn;
+        rc->pixel = pb + tid;
+        rc->b = s_b[tid];
+        rc->alpha = al;
+        rc->coef = co;
+        rc->dv = s_dv[tid];
+        for (int p = 0; p < n_o; ++p) rc->Tk[p] = s_T[p * kOwnMax + tid];
+      };
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-        long long bmin = block_min_ll(best);
-        if (threadIdx.x == 0) sel_offer(ctl, rd, bmin, cta);
-        if (bmin == LLONG_MAX) {
-          if (threadIdx.x == 0) rc->key = LLONG_MAX;
-        } else if (best == bmin) {
-          fill_record(a, rc, pix, best, 0.0, b_alpha, b_coef);
+        long long cand = kNoCand;
+        if (ok) {
+          const int pos = s_pos[tid];
+          if (pos >= t && gain_of(s_op, fn, f) - thr > 0.0) cand = ((long long)pos << kPixBits) | (pb + tid);
         }
+        key = block_min_ll(cand);
+        if (key != kNoCand && cand == key) fill(cand >> kPixBits, 0.0);
       } else {
+        double g = -INFINITY;
+        int pix = INT_MAX;
+        if (ok) {
+          g = gain_of(s_op, fn, f);
+          pix = pb + tid;
+        }
         double gb = g;
         int pb2 = pix;
         block_best(gb, pb2);
-        if (pb2 == INT_MAX) {
-          if (threadIdx.x == 0) { rc->key = LLONG_MAX; rc->gain = -INFINITY; rc->pixel = INT_MAX; }
-        } else if (pix == pb2) {
-          fill_record(a, rc, pix, 0, gb, b_alpha, b_coef);
+        if (pb2 != INT_MAX) {
+          key = pb2;
+          if (pix == pb2) fill(0, gb);
         }
       }
     }
     tick(0);
-    if (!grid_sync(ctl)) { failed = true; break; }
-    tick(1);
-    // ---- warp 0 picks the winning record; lane 0 forms the pivot while the
-    //      other lanes already gather beta_i = alpha_i x_i[k] (FIRST mode: k is
-    //      known from the selection cell before the record arrives)
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      int win = -1, k_pre = -1;
+    __syncthreads();
+    if (tid == 0) {
+      fence_acq_rel_gpu();  // release: the record and the earlier appends to X before the word
+      *reinterpret_cast<volatile unsigned long long*>(words + (size_t)cta * kSlotStride) =
+          ((unsigned long long)seq << kSeqShift) | (unsigned long long)key;
+    }
+    tick(12);
+    // ---- every CTA's word of this round
+    int k = -1, pos_k = 0;
+    {
+      long long kq = kNoCand;
+      if (tid < P) {
+        bool ok = true;
+        kq = poll_word(words + (size_t)tid * kSlotStride, seq, ok);
+        if (!ok) {
+          s_fail = 1;
+          latch_status(ctl, PNGF_ETIMEOUT);
+        }
+        fence_acq_rel_gpu();  // acquire: CTA q's record and appends to X
+      }
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-        unsigned long long key = sel_read(ctl, rd);
-        if (key != ~0ull) {
-          win = (int)(key & 1023u);
-          int pos = (int)(key >> 10);
-          k_pre = a.order ? a.order[(size_t)s * n + pos] : pos;
-          if ((unsigned)k_pre >= (unsigned)n) win = -2;
-          if ((unsigned)k_pre < (unsigned)n) {
-            for (int i = lane; i < r; i += 32) {
-              c128 al = a.xa[i];
-              float2 x = a.X[(size_t)k_pre * a.R + i];
-              float ax = (float)al.x, ay = (float)al.y;
-              s_beta[i] = make_float2(fmaf(ax, x.x, -ay * x.y), fmaf(ax, x.y, ay * x.x));
-            }
-          }
+        const long long kmin = block_min_ll(kq);
+        if (kmin != kNoCand) {
+          pos_k = (int)(kmin >> kPixBits);
+          k = (int)(kmin & ((1 << kPixBits) - 1));
         }
       } else {
         double g = -INFINITY;
-        int pix = INT_MAX, q_best = -1;
-        for (int q = lane; q < P; q += 32) {
-          const CandRecord* rq = rec_at(a, slot, q);
-          double gg = rq->gain;
-          int pp = rq->pixel;
-          if (pp != INT_MAX && better(gg, pp, g, pix)) { g = gg; pix = pp; q_best = q; }
+        int pix = INT_MAX;
+        if (kq != kNoCand) {
+          pix = (int)kq;
+          g = mrec_at(a, par, tid)->gain;
         }
-        for (int off = 16; off > 0; off >>= 1) {
-          double og = __shfl_xor_sync(0xffffffffu, g, off);
-          int op = __shfl_xor_sync(0xffffffffu, pix, off);
-          int oq = __shfl_xor_sync(0xffffffffu, q_best, off);
-          if (better(og, op, g, pix)) { g = og; pix = op; q_best = oq; }
-        }
-        if (q_best >= 0 && g - thr > 0.0) win = q_best;
-      }
-      if (lane == 0) {
-        s_k = win == -2 ? -2 : -1;
-        s_pos = 0;
-        if (win >= 0) {
-          CandRecord rw = *rec_at(a, slot, win);
-          s_k = rw.pixel;
-          s_pos = (int)rw.key;
-          pivot_from_record(rw, a.n_o, s_pv);
-          FOR_PORTS(p, a.n_o) s_o[p] = cfma(s_pv.coef, s_pv.Tk[p], s_o[p]);
-          s_f = objective_of(s_op, s_o);
-        }
-      }
-      if (a.mode == PNGF_BEST_IMPROVEMENT) {
-        __syncwarp();
-        const int kb = s_k;
-        if (kb >= 0)
-          for (int i = lane; i < r; i += 32) {
-            c128 al = a.xa[i];
-            float2 x = a.X[(size_t)kb * a.R + i];
-            float ax = (float)al.x, ay = (float)al.y;
-            s_beta[i] = make_float2(fmaf(ax, x.x, -ay * x.y), fmaf(ax, x.y, ay * x.x));
-          }
+        block_best(g, pix);
+        if (pix != INT_MAX && g - thr > 0.0) k = pix;
       }
     }
-    __syncthreads();
-    slot ^= 1;
-    ++rd;
-    const int k = s_k, pos_k = s_pos;
-    if (k == -2) {  // invalid visiting-order entry
-      status = PNGF_EINVAL;
+    ++round;
+    if (s_fail) {
+      failed = true;
       break;
     }
+    tick(1);
     if (k < 0) {
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
         n_evals += n - t;
@@ -246,9 +365,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         t = 0;
         acc_in_sweep = 0;
         if (a.order) {
-          setup_sweep(s);
-          if (!grid_sync(ctl)) { failed = true; break; }
-          if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
+          if (!setup_sweep(s)) { failed = true; break; }
+          __syncthreads();
         }
         tick(6);
         continue;
@@ -259,6 +377,32 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         break;
       }
     }
+    // ---- fetch, in parallel: the winner's record, beta_i = alpha_i x_i[k], W_lo(k, own)
+    if (tid < 32) {
+      const MixRecord* rw = mrec_at(a, par, owner_of(k, n, P));
+      if (lane == 0) {
+        s_pv.k = k;
+        s_pv.alpha = rw->alpha;
+        s_pv.coef = rw->coef;
+        s_f = rw->f_new;
+      } else if (lane <= n_o) {
+        s_pv.Tk[lane - 1] = rw->Tk[lane - 1];
+      } else if (lane >= 16 && lane < 16 + n_o) {
+        // S(new) exactly as the scorer formed it for its objective
+        const int p = lane - 16;
+        s_S[p] = cfma(rw->coef, rw->Tk[p], s_S[p]);
+      }
+    } else if (tid < 32 + r) {
+      const int i = tid - 32;
+      const float2 al = s_alpha[i], x = a.X[(size_t)k * R + i];
+      s_beta[i] = make_float2(fmaf(al.x, x.x, -al.y * x.y), fmaf(al.x, x.y, al.y * x.x));
+    } else if (tid >= 256 && tid < 256 + own) {
+      const int jl = tid - 256;
+      const c128 w = wlo_sym(a, k, pb + jl);
+      s_wk[jl] = make_float2((float)w.x, (float)w.y);
+    }
+    __syncthreads();
+    tick(2);
     // ---- keep the flip of pixel k
     if (!isfinite(s_f)) status = PNGF_ENUMERIC;
     if (a.mode == PNGF_FIRST_IMPROVEMENT) {
@@ -269,53 +413,114 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       ++sweeps_done;
     }
     ++acc_in_sweep;
-    if (cta == 0 && threadIdx.x == 0) {
-      if (n_acc < a.trace_cap) {
-        if (a.trace) {
-          int32_t* tr = a.trace + 4 * n_acc;
-          tr[0] = a.mode == PNGF_FIRST_IMPROVEMENT ? s : (int)n_acc;
-          tr[1] = pos_k;
-          tr[2] = k;
-          tr[3] = 0;
+    if (tid == 0) {
+      if (cta == 0) {
+        if (n_acc < a.trace_cap) {
+          if (a.trace) {
+            int32_t* tr = a.trace + 4 * n_acc;
+            tr[0] = a.mode == PNGF_FIRST_IMPROVEMENT ? s : (int)n_acc;
+            tr[1] = pos_k;
+            tr[2] = k;
+            tr[3] = 0;
+          }
+          if (a.trace_f) a.trace_f[n_acc] = s_f;
+        } else if (status == PNGF_OK) {
+          status = PNGF_ECAPACITY;
         }
-        if (a.trace_f) a.trace_f[n_acc] = s_f;
-      } else if (status == PNGF_OK) {
-        status = PNGF_ECAPACITY;
+        a.xa[r] = s_pv.alpha;
       }
-      a.xa[r] = s_pv.alpha;
+      s_alpha[r] = make_float2((float)s_pv.alpha.x, (float)s_pv.alpha.y);
     }
     ++n_acc;
-    tick(2);
-    mixed_accept_own(a, s_pv, s_beta, r, pb, pe);
+    // U2: a 16-lane group per own pixel forms the delayed sum in FP32 and the
+    // column entry c_j = W_lo(k, j) + sum_i beta_i x_i[j] (FP32)
+    {
+      const int g = tid >> 4, gl = tid & 15;
+      const unsigned half = 0xffffu << (tid & 16);
+      for (int jl = g; jl < own; jl += kThreads / 16) {
+        const float2* xj = Xs + jl * R;
+        float px = 0.f, py = 0.f;
+        for (int i = gl; i < r; i += 16) {
+          float2 b = s_beta[i], x = xj[i];
+          px = fmaf(b.x, x.x, fmaf(-b.y, x.y, px));
+          py = fmaf(b.x, x.y, fmaf(b.y, x.x, py));
+        }
+        for (int off = 8; off > 0; off >>= 1) {
+          px += __shfl_xor_sync(half, px, off);
+          py += __shfl_xor_sync(half, py, off);
+        }
+        if (gl == 0) s_sum[jl] = make_float2(s_wk[jl].x + px, s_wk[jl].y + py);
+      }
+    }
+    __syncthreads();
+    tick(13);
+    // U3: FP64 state update; quantity q (0: diag and the appended column,
+    // 1: e, 2 + p: row p of T') on warps of different sub-partitions
+    {
+      const int nq = 2 + n_o;
+      for (int q = warp & 3; q < nq; q += 4)
+        for (int jl = (warp >> 2) * 32 + lane; jl < own; jl += kThreads / 4) {
+          const float2 cf = s_sum[jl];
+          const c128 cj = mk((double)cf.x, (double)cf.y);
+          if (q == 0) {
+            const int j = pb + jl;
+            Xs[jl * R + r] = cf;
+            a.X[(size_t)j * R + r] = cf;
+            s_diag[jl] = cfma(cmul(s_pv.alpha, cj), cj, s_diag[jl]);
+            if (j == k) {
+              const unsigned char nb = s_b[jl] ^ 1;
+              s_b[jl] = nb;
+              a.b[j] = nb;
+              a.v[j] = nb ? s_dv[jl] : mk(0.0, 0.0);
+            }
+          } else if (q == 1) {
+            s_e[jl] = cfma(s_pv.coef, cj, s_e[jl]);
+          } else {
+            c128* tq = s_T + (q - 2) * kOwnMax + jl;
+            *tq = cfma(cmul(s_pv.alpha, cj), s_pv.Tk[q - 2], *tq);
+          }
+        }
+    }
+    __syncthreads();
     ++r;
     ++since_refresh;
-    __syncthreads();
     tick(4);
-    if (r == a.R) {
+    if (r == R) {
       if (!flush()) { failed = true; break; }
       tick(3);
       if (a.refresh_k > 0 && since_refresh >= a.refresh_k) {
         since_refresh = 0;
         ++n_refresh;
+        store_et(false);
+        __syncthreads();
         refresh_x(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(8);
-        refresh_residual(a, pb, pe);
+        // the delayed set is empty here: its shared memory holds the active-pixel list
+        const int m_act = refresh_residual(a, pb, pe, reinterpret_cast<int*>(work));
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(9);
-        refresh_correct(a, pb, pe);
+        (void)m_act;
+        correct_tiles(a, reinterpret_cast<float*>(work));
+        tick(14);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        tick(15);
+        correct_finish(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(10);
         ports_partial(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(11);
-        if (threadIdx.x == 0) {
-          FOR_PORTS(p, a.n_o) {
+        load_et();
+        if (tid == 0) {
+          c128 o[kMaxPorts];
+          FOR_PORTS(p, n_o) {
             c128 acc = mk(0.0, 0.0);
-            for (int q = 0; q < P; ++q) acc = cadd(acc, a.opart[(size_t)q * a.n_o + p]);
-            s_o[p] = cadd(a.co[p], acc);
+            for (int q = 0; q < P; ++q) acc = cadd(acc, a.opart[(size_t)q * n_o + p]);
+            o[p] = cadd(a.co[p], acc);
+            s_S[p] = cmul(csub(o[p], s_op.off[p]), s_op.scale[p]);
           }
-          s_f = objective_of(s_op, s_o);
+          s_f = objective_of(s_op, o);
         }
         __syncthreads();
         tick(5);
@@ -330,13 +535,13 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       t = 0;
       acc_in_sweep = 0;
       if (a.order) {
-        if (!grid_sync(ctl)) { failed = true; break; }
-        setup_sweep(s);
-        if (!grid_sync(ctl)) { failed = true; break; }
-        if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) { status = PNGF_EINVAL; break; }
+        if (!setup_sweep(s)) { failed = true; break; }
+        __syncthreads();
       }
     }
   }
+  __syncthreads();
+  store_et(true);
   if (a.tensor_fold) {
     if (failed && threadIdx.x < 128) {
       // give what this CTA issued a bounded time to land before the free
@@ -349,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   }
   if (cta == 0 && threadIdx.x == 0) {
     if (failed) status = PNGF_ETIMEOUT;
-    FOR_PORTS(p, a.n_o) ctl->o[p] = s_o[p];
+    FOR_PORTS(p, n_o) ctl->o[p] = cadd(cmul(s_S[p], s_iscale[p]), s_op.off[p]);
     ctl->f = s_f;
     ctl->since_refresh = since_refresh;
     ctl->r_delay = r;
@@ -450,7 +655,11 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
-constexpr size_t kMixedSmem = kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM;
+constexpr size_t kMixedWork = kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM;
+static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
+static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
+static_assert(kMixedWork >= ct_smem_bytes(1 + kMaxPorts), "tile stage of the refresh correction");
+constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
 
 static int mixed_grid(pngf_ctx* c) {
   static bool attr = false;
@@ -479,11 +688,12 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   a.trace_cap = trace_cap;
   a.counters = counters;
   Control* ctl = a.ctl;
+  int grid = mixed_grid(c);
+  if ((c->cfg.n_d + grid - 1) / grid > kOwnMax) return PNGF_EINVAL;  // own-pixel state is shared memory
   cudaError_t err = cudaMemsetAsync(&ctl->bar_count, 0, 2 * sizeof(unsigned), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
-  err = cudaMemsetAsync(&ctl->sel[0], 0xff, sizeof(ctl->sel), c->stream);
+  err = cudaMemsetAsync(a.slots, 0, (size_t)2 * grid * kSlotStride * sizeof(unsigned long long), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
-  int grid = mixed_grid(c);
   void* params[] = {&a};
   err = cudaLaunchCooperativeKernel((const void*)dbs_mixed_kernel, dim3(grid), dim3(kThreads), params, kMixedSmem,
                                     c->stream);
