@@ -409,7 +409,7 @@ def main():
         phase_names = ["score", "wait_after_score", "select_pivot_gather", "wait_or_flush",
                        "update", "refresh", "sweep_setup", "kernel_total", "refresh_x", "refresh_residual",
                        "refresh_correct", "refresh_ports", "publish", "update_delayed_sum",
-                       "refresh_correct_tiles", "refresh_sync_after_tiles"]
+                       "unused14", "unused15"]
         phase_ms = {nm: float(cv) / (mhz * 1e3) for nm, cv in zip(phase_names, cyc)}
         ms = t0.elapsed_time(t1)
         ms_max = dist.max(torch, ms, dev)

@@ -61,7 +61,7 @@ Layout make_layout(const pngf_config& cfg) {
   L.tcimg = take(L.tcimg_bytes);
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
-  L.cpart = take((size_t)ct_tiles((int)n) * 2 * (1 + n_o) * CT * sizeof(float2));  // refresh tile partials
+  L.actg = take(n * sizeof(int));  // active-pixel list of the refresh
   L.ipiv = take(2 * n * sizeof(int));
   L.snapW = take(L.snapW_bytes);
   L.snapState = take(L.state_bytes + sizeof(Control));

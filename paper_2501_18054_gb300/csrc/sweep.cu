@@ -229,25 +229,19 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       refresh_x(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(8);
-      refresh_residual(a, pb, pe, act_smem);
+      const int m_act = refresh_residual(a, pb, pe, act_smem);
+      const int t_end = count_below(act_smem, m_act, pe - 1);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(9);
-      correct_tiles(a, reinterpret_cast<float*>(act_smem));
-      if (!grid_sync(ctl)) { failed = true; break; }
-      correct_finish(a, pb, pe);
+      correct_strips<false>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(act_smem),
+                            (int)dynamic_smem_bytes());
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(10);
       ports_partial(a, pb, pe);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(11);
-      if (threadIdx.x == 0) {
-        FOR_PORTS(p, a.n_o) {
-          c128 acc = mk(0.0, 0.0);
-          for (int q = 0; q < P; ++q) acc = cadd(acc, a.opart[(size_t)q * a.n_o + p]);
-          s_o[p] = cadd(a.co[p], acc);
-        }
-        s_f = objective_of(s_op, s_o);
-      }
+      ports_total(a, s_o);
+      if (threadIdx.x == 0) s_f = objective_of(s_op, s_o);
       __syncthreads();
       // no CTA rewrites opart before the next refresh, many barriers later
       tick(5);
@@ -348,9 +342,9 @@ __global__ void __launch_bounds__(kThreads) accept_update_kernel(SweepArgs a, co
 
 }  // namespace
 
-// active-pixel list of the refresh residual, then the tile stage of the correction
+// active-pixel list of the refresh residual, then the staging of the correction
 static size_t fp64_smem(int n) {
-  const size_t act = (size_t)n * sizeof(int), ct = ct_smem_bytes(1 + kMaxPorts);
+  const size_t act = (size_t)n * sizeof(int), ct = (size_t)110 * 1024;  // room to stage x2 of n_d = 4096 at once
   return act > ct ? act : ct;
 }
 

@@ -48,7 +48,7 @@ struct SweepArgs {
   c128* xa;   // R coefficients alpha_i
   void* rec;  // [2][P] candidate records
   unsigned long long* slots;  // [2][P] round words of the mixed search, 128 B apart
-  float2* cpart;              // tile partial sums of the refresh correction
+  int* actg;                  // n: active-pixel list of the last refresh (written by CTA 0)
 };
 
 // a CTA's candidate of one scoring round, with the state the pivot needs
@@ -374,6 +374,16 @@ __device__ int active_list(const SweepArgs& a, int* act) {
   return s_m;
 }
 
+// number of entries of the ascending list act[0, m) below v (shared memory)
+__device__ __forceinline__ int count_below(const int* act, int m, int v) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (act[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // R1: residuals of own rows (row j of G dotted with x), and x2 = v.r.  With
 // act (shared memory, room for n entries) only the columns of G at pixels
 // with b_i = 1 are visited: x vanishes elsewhere, so the FP64 work follows the
@@ -382,6 +392,8 @@ template <int NV>
 __device__ __noinline__ int refresh_residual_t(const SweepArgs& a, int pb, int pe, int* act) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int m = act ? active_list(a, act) : a.n;
+  if (act && blockIdx.x == 0)  // for the correction, after the next grid barrier
+    for (int t = threadIdx.x; t < m; t += blockDim.x) a.actg[t] = act[t];
   for (int j = pb + warp; j < pe; j += nw) {
     const c128* g = a.G + (size_t)j * a.n;
     c128 acc[NV];
@@ -442,8 +454,12 @@ __device__ __forceinline__ f2c f2sum(f2c v) {
 
 // element (i, j) of the maintained W with i <= j, as FP32 (FP64 storage or the
 // planar FP32 copy of the mixed path)
+// (MIXED is a template parameter: a runtime test would leave the FP64
+// path's conversions in the mixed loops as predicated-off FP64 instructions,
+// which still occupy the FP64 pipe.)
+template <bool MIXED>
 __device__ __forceinline__ f2c w_upper(const SweepArgs& a, int i, int j) {
-  if (a.mixed) {
+  if (MIXED) {
     size_t o = (size_t)i * a.ldl + j;
     return f2c{a.Wr[o], a.Wi[o]};
   }
@@ -453,8 +469,9 @@ __device__ __forceinline__ f2c w_upper(const SweepArgs& a, int i, int j) {
 // four consecutive elements W(j, i0 .. i0+3) of the maintained W as FP32
 // (i0 % 4 == 0; rows are padded to a multiple of 4 so the read stays inside
 // the row; elements past n are masked by the caller)
+template <bool MIXED>
 __device__ __forceinline__ void w_row4(const SweepArgs& a, int j, int i0, f2c w[4]) {
-  if (a.mixed) {
+  if (MIXED) {
     const size_t o = (size_t)j * a.ldl + i0;
     const float4 re = *reinterpret_cast<const float4*>(a.Wr + o);
     const float4 im = *reinterpret_cast<const float4*>(a.Wi + o);
@@ -471,7 +488,7 @@ __device__ __forceinline__ void w_row4(const SweepArgs& a, int j, int i0, f2c w[
 
 // R2, upper part: one warp per own row j, sum over i >= j of W[j][i] x2_i
 // with four-wide row reads, four chunks in flight per lane.
-template <int NV>
+template <int NV, bool MIXED>
 __device__ __forceinline__ void correct_upper(const SweepArgs& a, int pb, int pe) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = a.n;
@@ -483,7 +500,7 @@ __device__ __forceinline__ void correct_upper(const SweepArgs& a, int pb, int pe
 #pragma unroll 4
     for (int i0 = ib + 4 * lane; i0 < n; i0 += 128) {
       f2c w[4];
-      w_row4(a, j, i0, w);
+      w_row4<MIXED>(a, j, i0, w);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u;
@@ -511,11 +528,11 @@ __device__ __forceinline__ void correct_upper(const SweepArgs& a, int pb, int pe
 // to |r| (classic mixed-precision iterative refinement), so it runs in FP32
 // arithmetic and is added to r in FP64.  x2 = v.r vanishes where b_i = 0, so
 // with the active list act[0, m) only those rows of the strip are read.
-template <int NV>
+template <int NV, bool MIXED>
 __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int pe, const int* act, int m) {
   __shared__ f2c red[kThreads / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  correct_upper<NV>(a, pb, pe);
+  correct_upper<NV, MIXED>(a, pb, pe);
   __syncthreads();
   // lower part: columns of this CTA in blocks of 32 (lane = column), the rows
   // above spread over the warps, eight rows in flight per warp
@@ -547,7 +564,7 @@ __device__ __noinline__ void refresh_correct_t(const SweepArgs& a, int pb, int p
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         w[u] = f2c{0.f, 0.f};
-        if (ii[u] >= 0 && colok && ii[u] < j) w[u] = w_upper(a, ii[u], j);
+        if (ii[u] >= 0 && colok && ii[u] < j) w[u] = w_upper<MIXED>(a, ii[u], j);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -599,204 +616,194 @@ __device__ int refresh_residual(const SweepArgs& a, int pb, int pe, int* act = n
 }
 
 // act, m: the active list left by refresh_residual in this CTA, or nullptr
-__device__ void refresh_correct(const SweepArgs& a, int pb, int pe, const int* act = nullptr, int m = 0) {
+template <bool MIXED>
+__device__ void refresh_correct_m(const SweepArgs& a, int pb, int pe, const int* act, int m) {
   switch (a.n_o) {
-    case 1: refresh_correct_t<2>(a, pb, pe, act, m); break;
-    case 2: refresh_correct_t<3>(a, pb, pe, act, m); break;
-    case 3: refresh_correct_t<4>(a, pb, pe, act, m); break;
-    case 4: refresh_correct_t<5>(a, pb, pe, act, m); break;
-    case 5: refresh_correct_t<6>(a, pb, pe, act, m); break;
-    case 6: refresh_correct_t<7>(a, pb, pe, act, m); break;
-    case 7: refresh_correct_t<8>(a, pb, pe, act, m); break;
-    default: refresh_correct_t<9>(a, pb, pe, act, m); break;
+    case 1: refresh_correct_t<2, MIXED>(a, pb, pe, act, m); break;
+    case 2: refresh_correct_t<3, MIXED>(a, pb, pe, act, m); break;
+    case 3: refresh_correct_t<4, MIXED>(a, pb, pe, act, m); break;
+    case 4: refresh_correct_t<5, MIXED>(a, pb, pe, act, m); break;
+    case 5: refresh_correct_t<6, MIXED>(a, pb, pe, act, m); break;
+    case 6: refresh_correct_t<7, MIXED>(a, pb, pe, act, m); break;
+    case 7: refresh_correct_t<8, MIXED>(a, pb, pe, act, m); break;
+    default: refresh_correct_t<9, MIXED>(a, pb, pe, act, m); break;
   }
 }
-
-// ---------------------------------------------------------------- refresh correction, tiled
-// The persistent kernels form y = W x2 (x2 = v.r, W symmetric with its upper
-// triangle current) by 64 x 64 tiles of the upper triangle: a tile (I, J),
-// I <= J, is read once and yields both its row sums W[I, J] x2[J] (for block
-// I) and its column sums W[I, J]^T x2[I] (for block J); on a diagonal tile the
-// row sums take the upper part including the diagonal and the column sums
-// the strict upper part.  Partial sums go to cpart, tile by tile, and the
-// owner of a row adds them in a fixed order (deterministic, no atomics).
-constexpr int CT = 64;
-
-__host__ __device__ __forceinline__ long long ct_tiles(int n) {
-  const long long tn = (n + CT - 1) / CT;
-  return tn * (tn + 1) / 2;
-}
-__device__ __forceinline__ long long ct_index(int I, int J, int tn) {
-  return (long long)I * tn - (long long)I * (I - 1) / 2 + (J - I);
-}
-// cpart[((t * 2 + side) * NV + q) * CT + i], side 0: row sums, 1: column sums
-__device__ __forceinline__ float2* ct_part(const SweepArgs& a, long long t, int side, int q, int nv) {
-  return a.cpart + (((size_t)t * 2 + side) * nv + q) * CT;
-}
-// shared memory of correct_tiles_t: x2 of both blocks and one column-sum stage
-__host__ __device__ constexpr size_t ct_smem_bytes(int nv) {
-  return (size_t)2 * nv * CT * sizeof(float2) + (size_t)(kThreads / 32) * CT * sizeof(float2);
+__device__ void refresh_correct(const SweepArgs& a, int pb, int pe, const int* act = nullptr, int m = 0) {
+  if (a.mixed) refresh_correct_m<true>(a, pb, pe, act, m);
+  else refresh_correct_m<false>(a, pb, pe, act, m);
 }
 
-template <int NV>
-__device__ __noinline__ void correct_tiles_t(const SweepArgs& a, float* smem) {
-  const int n = a.n, tn = (n + CT - 1) / CT;
-  const long long T = ct_tiles(n);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tx = tid & 15, ty = tid >> 4;  // columns 4 tx .. 4 tx + 3, rows 2 ty, 2 ty + 1
-  float2* xJ = reinterpret_cast<float2*>(smem);  // [NV][CT]
-  float2* xI = xJ + NV * CT;                     // [NV][CT]
-  float2* cst = xI + NV * CT;                    // [warps][CT]
-  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
-    int I, J;
-    tri_rc(t, tn, I, J);
-    const int i0 = I * CT, j0 = J * CT;
-    const bool diag = I == J;
-    __syncthreads();
-    for (int q = tid; q < NV * CT; q += blockDim.x) {
-      const int v = q / CT, c = q - v * CT;
-      xJ[q] = j0 + c < n ? x2f(a, v)[j0 + c] : make_float2(0.f, 0.f);
-      xI[q] = i0 + c < n ? x2f(a, v)[i0 + c] : make_float2(0.f, 0.f);
+// ---------------------------------------------------------------- refresh correction, strips
+// y = W x2 for the own rows (W symmetric, upper triangle current, x2 = v.r):
+// the upper part sum_{i>=j} W[j][i] x2_i streams the own rows (one warp per
+// row, four-wide reads), the lower part sum_{i<j} W[i][j] x2_i streams the
+// rows above the own column strip, only those with b_i = 1 (x2 vanishes
+// elsewhere).  x2 is staged in shared memory (all of it when it fits, else
+// chunk by chunk) so that the inner loops read nothing but W from memory.
+constexpr int CS_UNROLL = 16;  // lower part: rows in flight per warp
+
+// bytes of dynamic shared memory of the running launch
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned b;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(b));
+  return b;
+}
+
+// least shared memory the strips need (one 128-column chunk, 128 rows)
+__host__ __device__ constexpr size_t cs_min_smem_bytes(int nv) {
+  return (size_t)(kThreads / 32) * 32 * nv * sizeof(float2) + (size_t)nv * 128 * sizeof(float2) +
+         128 * (sizeof(int) + nv * sizeof(float2));
+}
+
+// act: the ascending active-pixel list in global memory (or nullptr: every
+// row), t_end: the number of its entries below pe - 1; smem: smem_bytes of
+// shared memory
+template <int NV, bool MIXED>
+__device__ __noinline__ void correct_strips_t(const SweepArgs& a, int pb, int pe, const int* act, int t_end,
+                                              float* smem, int smem_bytes) {
+  const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  float2* red = reinterpret_cast<float2*>(smem);  // [warps][NV][32]
+  float2* xs = red + nw * NV * 32;                 // staged x2
+  const int avail = smem_bytes - nw * NV * 32 * (int)sizeof(float2);
+  // ---- upper part: rows g0 + warp of each group of nw own rows; chunks of cw columns
+  const int n128 = (n + 127) & ~127;
+  const int cw = min(n128, avail / (NV * (int)sizeof(float2)) / 128 * 128);
+  const bool whole = cw >= n128;  // x2 staged once for every row group
+  for (int g0 = pb; g0 < pe; g0 += nw) {
+    const int j = g0 + warp;
+    f2c acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
+    const int cstart = whole ? 0 : (g0 & ~127);
+    for (int c0 = cstart; c0 < n; c0 += cw) {
+      if (!whole || g0 == pb) {
+        __syncthreads();
+        // column cc of the chunk at (cc & 3) * (cw / 4) + (cc >> 2): lanes read consecutive words
+        for (int e = tid; e < NV * cw; e += blockDim.x) {
+          const int q = e / cw, cc = e - q * cw, c = c0 + cc;
+          xs[q * cw + (cc & 3) * (cw >> 2) + (cc >> 2)] = c < n ? x2f(a, q)[c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+      }
+      if (j < pe) {
+        const int kb = max(0, ((j & ~3) - c0) >> 7), ke = min(cw, n - c0 + 127) >> 7;
+        for (int k0 = kb; k0 < ke; k0 += 8) {  // eight four-wide reads in flight per lane
+          f2c w[8][4];
+#pragma unroll
+          for (int u8 = 0; u8 < 8; ++u8) {
+            const int col = c0 + 128 * (k0 + u8) + 4 * lane;
+            if (k0 + u8 < ke && col + 3 >= j && col < n) {
+              w_row4<MIXED>(a, j, col, w[u8]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) w[u8][u] = f2c{0.f, 0.f};
+            }
+          }
+#pragma unroll
+          for (int u8 = 0; u8 < 8; ++u8) {
+            const int k = k0 + u8;
+            if (k < ke) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int i = c0 + 128 * k + 4 * lane + u;
+                if (i >= j && i < n) {
+#pragma unroll
+                  for (int q = 0; q < NV; ++q) {
+                    const float2 x = xs[q * cw + u * (cw >> 2) + 32 * k + lane];
+                    acc[q] = f2fma(w[u8][u], f2c{x.x, x.y}, acc[q]);
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
     }
-    // the tile in registers (masked entries are zero)
-    f2c w[2][4];
-    const int cg = j0 + 4 * tx;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int rg = i0 + 2 * ty + u;
-      if (rg < n && cg < n) {
-        w_row4(a, rg, cg, w[u]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) w[u][c] = f2c{0.f, 0.f};
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (cg + c >= n || (diag && cg + c < rg)) w[u][c] = f2c{0.f, 0.f};  // upper part only
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int q = 0; q < NV; ++q) {
-      // row sums over this thread's four columns, then over the 16 column groups
-      f2c rs[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        rs[u] = f2c{0.f, 0.f};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float2 x = xJ[q * CT + 4 * tx + c];
-          rs[u] = f2fma(w[u][c], f2c{x.x, x.y}, rs[u]);
-        }
-#pragma unroll
-        for (int off = 1; off < 16; off <<= 1) {
-          rs[u].x += __shfl_xor_sync(0xffffffffu, rs[u].x, off);
-          rs[u].y += __shfl_xor_sync(0xffffffffu, rs[u].y, off);
-        }
-      }
-      if (tx == 0) {
-        float2* pr = ct_part(a, t, 0, q, NV);
-        pr[2 * ty] = make_float2(rs[0].x, rs[0].y);
-        pr[2 * ty + 1] = make_float2(rs[1].x, rs[1].y);
-      }
-      // column sums over this thread's two rows (strict upper part on a diagonal tile)
-      f2c cs[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        cs[c] = f2c{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (diag && cg + c == i0 + 2 * ty + u) continue;  // the diagonal belongs to the row sums
-          const float2 x = xI[q * CT + 2 * ty + u];
-          cs[c] = f2fma(w[u][c], f2c{x.x, x.y}, cs[c]);
-        }
-        cs[c].x += __shfl_xor_sync(0xffffffffu, cs[c].x, 16);
-        cs[c].y += __shfl_xor_sync(0xffffffffu, cs[c].y, 16);
-      }
-      if (lane < 16)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cst[warp * CT + 4 * tx + c] = make_float2(cs[c].x, cs[c].y);
-      __syncthreads();
-      if (tid < CT) {
-        float sx = 0.f, sy = 0.f;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
-          sx += cst[w2 * CT + tid].x;
-          sy += cst[w2 * CT + tid].y;
-        }
-        ct_part(a, t, 1, q, NV)[tid] = make_float2(sx, sy);
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// after a grid barrier: e, T of own rows += r + y, y summed from the tile
-// partials in a fixed order (one warp per row, lanes over the tiles)
-template <int NV>
-__device__ __noinline__ void correct_finish_t(const SweepArgs& a, int pb, int pe) {
-  const int n = a.n, tn = (n + CT - 1) / CT;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = pb + warp; j < pe; j += nw) {
-    const int B = j / CT, rho = j - B * CT;
-    const int nterm = tn + 1;  // row sums of tiles (B, J >= B), column sums of tiles (I <= B, B)
-    float sx[NV], sy[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sx[q] = sy[q] = 0.f;
-#pragma unroll 4
-    for (int u = lane; u < nterm; u += 32) {
-      const float2* base = u < tn - B ? ct_part(a, ct_index(B, B + u, tn), 0, 0, NV)
-                                      : ct_part(a, ct_index(u - (tn - B), B, tn), 1, 0, NV);
+    if (j < pe) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const float2 p = base[q * CT + rho];
-        sx[q] += p.x;
-        sy[q] += p.y;
+        const f2c sum = f2sum(acc[q]);
+        if (lane == 0) rvec(a, 3, q)[j] = mk(sum.x, sum.y);
       }
     }
+  }
+  // ---- lower part: own columns in blocks of 32 (lane = column), active rows i < pe - 1
+  const int rcap = min(max(t_end, 1), avail / (int)(sizeof(int) + NV * sizeof(float2)));
+  int* rows = reinterpret_cast<int*>(xs + NV * rcap);
+  for (int cb = pb; cb < pe; cb += 32) {
+    const int j = cb + lane;
+    const bool colok = j < pe;
+    f2c acc[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      for (int off = 16; off > 0; off >>= 1) {
-        sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], off);
-        sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], off);
-      }
-    }
-    if (lane < NV) {  // lane q updates vector q (e for q = 0, row q - 1 of T otherwise)
-      float fx = 0.f, fy = 0.f;
-#pragma unroll
-      for (int q = 0; q < NV; ++q)
-        if (q == lane) {
-          fx = sx[q];
-          fy = sy[q];
+    for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
+    for (int t0 = 0; t0 < t_end; t0 += rcap) {
+      const int cnt = min(rcap, t_end - t0);
+      if (cb == pb || cnt < t_end) {  // staged once when every row fits
+        __syncthreads();
+        for (int e = tid; e < cnt; e += blockDim.x) rows[e] = act ? act[t0 + e] : t0 + e;
+        __syncthreads();
+        for (int e = tid; e < NV * cnt; e += blockDim.x) {
+          const int q = e / cnt, tt = e - q * cnt;
+          xs[q * rcap + tt] = x2f(a, q)[rows[tt]];
         }
-      const c128 d = cadd(rvec(a, 0, lane)[j], mk((double)fx, (double)fy));
-      c128* dst = lane == 0 ? a.e + j : a.T + (size_t)(lane - 1) * a.ldt + j;
+        __syncthreads();
+      }
+      for (int tt = warp; tt < cnt; tt += CS_UNROLL * nw) {
+        f2c w[CS_UNROLL];
+#pragma unroll
+        for (int u = 0; u < CS_UNROLL; ++u) {
+          const int t2 = tt + u * nw;
+          w[u] = f2c{0.f, 0.f};
+          if (t2 < cnt) {
+            const int i = rows[t2];
+            if (colok && i < j) w[u] = w_upper<MIXED>(a, i, j);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < CS_UNROLL; ++u) {
+          const int t2 = tt + u * nw;
+          if (t2 < cnt) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const float2 x = xs[q * rcap + t2];
+              acc[q] = f2fma(w[u], f2c{x.x, x.y}, acc[q]);
+            }
+          }
+        }
+      }
+    }
+    // sum the warps' column partials, then e, T += r + upper + lower
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[(warp * NV + q) * 32 + lane] = make_float2(acc[q].x, acc[q].y);
+    __syncthreads();
+    if (warp < NV && colok) {
+      const int q = warp;
+      float sx = 0.f, sy = 0.f;
+      for (int w2 = 0; w2 < nw; ++w2) {
+        sx += red[(w2 * NV + q) * 32 + lane].x;
+        sy += red[(w2 * NV + q) * 32 + lane].y;
+      }
+      const c128 d = cadd(rvec(a, 0, q)[j], cadd(rvec(a, 3, q)[j], mk((double)sx, (double)sy)));
+      c128* dst = q == 0 ? a.e + j : a.T + (size_t)(q - 1) * a.ldt + j;
       *dst = cadd(*dst, d);
     }
+    __syncthreads();
   }
 }
 
-__device__ void correct_tiles(const SweepArgs& a, float* smem) {
+template <bool MIXED>
+__device__ void correct_strips(const SweepArgs& a, int pb, int pe, const int* act, int t_end, float* smem,
+                               int smem_bytes) {
   switch (a.n_o) {
-    case 1: correct_tiles_t<2>(a, smem); break;
-    case 2: correct_tiles_t<3>(a, smem); break;
-    case 3: correct_tiles_t<4>(a, smem); break;
-    case 4: correct_tiles_t<5>(a, smem); break;
-    case 5: correct_tiles_t<6>(a, smem); break;
-    case 6: correct_tiles_t<7>(a, smem); break;
-    case 7: correct_tiles_t<8>(a, smem); break;
-    default: correct_tiles_t<9>(a, smem); break;
-  }
-}
-
-__device__ void correct_finish(const SweepArgs& a, int pb, int pe) {
-  switch (a.n_o) {
-    case 1: correct_finish_t<2>(a, pb, pe); break;
-    case 2: correct_finish_t<3>(a, pb, pe); break;
-    case 3: correct_finish_t<4>(a, pb, pe); break;
-    case 4: correct_finish_t<5>(a, pb, pe); break;
-    case 5: correct_finish_t<6>(a, pb, pe); break;
-    case 6: correct_finish_t<7>(a, pb, pe); break;
-    case 7: correct_finish_t<8>(a, pb, pe); break;
-    default: correct_finish_t<9>(a, pb, pe); break;
+    case 1: correct_strips_t<2, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 2: correct_strips_t<3, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 3: correct_strips_t<4, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 4: correct_strips_t<5, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 5: correct_strips_t<6, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 6: correct_strips_t<7, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    case 7: correct_strips_t<8, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
+    default: correct_strips_t<9, MIXED>(a, pb, pe, act, t_end, smem, smem_bytes); break;
   }
 }
 
@@ -820,6 +827,24 @@ __device__ __noinline__ void ports_partial(const SweepArgs& a, int pb, int pe) {
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s = cadd(s, red[threadIdx.x][q]);
     a.opart[(size_t)blockIdx.x * a.n_o + threadIdx.x] = s;
   }
+}
+
+// o_p = c_o,p + sum over the CTAs of their partial sums (after a grid
+// barrier): warp p adds port p's partials in a fixed lane order and tree, so
+// every CTA obtains the same value; the FP64 adds run on one warp per port.
+__device__ void ports_total(const SweepArgs& a, c128* o_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < a.n_o) {
+    const int p = warp;
+    c128 acc = mk(0.0, 0.0);
+    for (int q = lane; q < (int)gridDim.x; q += 32) acc = cadd(acc, a.opart[(size_t)q * a.n_o + p]);
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) o_out[p] = cadd(a.co[p], acc);
+  }
+  __syncthreads();
 }
 
 SweepArgs make_args(pngf_ctx* c) {
@@ -859,7 +884,7 @@ SweepArgs make_args(pngf_ctx* c) {
   a.xa = at<c128>(c, L.xa);
   a.rec = c->ws + L.rec;
   a.slots = at<unsigned long long>(c, L.slots);
-  a.cpart = at<float2>(c, L.cpart);
+  a.actg = at<int>(c, L.actg);
   a.tensor_fold = c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold;
   a.tcimgA = reinterpret_cast<unsigned char*>(c->ws) + L.tcimg;
   a.tcimgB = a.tcimgA + L.tcimgA_bytes;

@@ -79,11 +79,14 @@ __device__ __forceinline__ MixRecord* mrec_at(const SweepArgs& a, int par, int q
 
 __device__ __forceinline__ int owner_of(int k, int n, int P) { return (int)(((long long)(k + 1) * P - 1) / n); }
 
-// objective of scaled amplitudes S (w_p |S_p|^2 summed, or w_p (1 - |S_p|)^2 summed)
-__device__ __forceinline__ double objective_term_a2(const ObjParams& op, int p, double a2) {
-  if (op.kind == PNGF_OBJ_MAX_WEIGHTED_POWER) return op.w[p] * a2;
-  double m = 1.0 - sqrt(a2);
-  return op.w[p] * (m * m);
+// acc + the objective term of one port from |S_p|^2 (w_p |S_p|^2, or
+// w_p (1 - |S_p|)^2); the objective kind is a template parameter so that the
+// other kind's FP64 instructions are not issued predicated-off per pixel
+template <int OBJ>
+__device__ __forceinline__ double obj_acc(double w, double a2, double acc) {
+  if (OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER) return fma(w, a2, acc);
+  const double m = 1.0 - sqrt(a2);
+  return fma(w, m * m, acc);
 }
 
 // waits (bounded) for CTA q's word of round `seq`; returns its key
@@ -100,6 +103,7 @@ __device__ __forceinline__ long long poll_word(const unsigned long long* w, unsi
   }
 }
 
+template <int OBJ>
 __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   extern __shared__ float dyn_smem[];
   const int P = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
@@ -121,11 +125,12 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ float2 s_wk[kOwnMax], s_sum[kOwnMax];
   __shared__ float2 s_beta[kMaxDelay], s_alpha[kMaxDelay];
   __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
+  __shared__ c128 s_o[kMaxPorts];      // port amplitudes after a refresh
   __shared__ c128 s_iscale[kMaxPorts];  // 1 / scale_p
   __shared__ double s_f;
   __shared__ Pivot s_pv;
   __shared__ ObjParams s_op;
-  __shared__ int s_fail;
+  __shared__ int s_fail, s_bad;
   float2* Xs = reinterpret_cast<float2*>(work);  // [own][R] delayed rows, between folds
   const int R = a.R;
   int r = ctl->r_delay;
@@ -252,6 +257,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   while (!failed && status != PNGF_EINVAL) {
     const double f = s_f;
     const double thr = accept_threshold(s_op, f);
+    // improving: f_new > f + thr (maximised) or f_new < f - thr (minimised)
+    const double fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? f + thr : f - thr;
     const int par = (int)(round & 1);
     const unsigned seq = (unsigned)((round + 1) & kSeqMask);
     unsigned long long* words = a.slots + (size_t)par * P * kSlotStride;
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           co = cmul(al, s_e[tid]);
 #pragma unroll 1
           for (int p = 0; p < n_o; ++p)
-            fn += objective_term_a2(s_op, p, cabs2(cfma(co, s_T[p * kOwnMax + tid], s_S[p])));
+            fn = obj_acc<OBJ>(s_op.w[p], cabs2(cfma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
           ok = true;
         }
       }
@@ -291,7 +298,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         long long cand = kNoCand;
         if (ok) {
           const int pos = s_pos[tid];
-          if (pos >= t && gain_of(s_op, fn, f) - thr > 0.0) cand = ((long long)pos << kPixBits) | (pb + tid);
+          const bool improving = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fn > fthr : fn < fthr;
+          if (pos >= t && improving) cand = ((long long)pos << kPixBits) | (pb + tid);
         }
         key = block_min_ll(cand);
         if (key != kNoCand && cand == key) fill(cand >> kPixBits, 0.0);
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         double g = -INFINITY;
         int pix = INT_MAX;
         if (ok) {
-          g = gain_of(s_op, fn, f);
+          g = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fn - f : f - fn;
           pix = pb + tid;
         }
         double gb = g;
@@ -377,44 +385,41 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         break;
       }
     }
-    // ---- fetch, in parallel: the winner's record, beta_i = alpha_i x_i[k], W_lo(k, own)
-    if (tid < 32) {
-      const MixRecord* rw = mrec_at(a, par, owner_of(k, n, P));
-      if (lane == 0) {
-        s_pv.k = k;
-        s_pv.alpha = rw->alpha;
-        s_pv.coef = rw->coef;
-        s_f = rw->f_new;
-      } else if (lane <= n_o) {
-        s_pv.Tk[lane - 1] = rw->Tk[lane - 1];
-      } else if (lane >= 16 && lane < 16 + n_o) {
-        // S(new) exactly as the scorer formed it for its objective
-        const int p = lane - 16;
-        s_S[p] = cfma(rw->coef, rw->Tk[p], s_S[p]);
+    // ---- fetch, in parallel: the winner's record, beta_i = alpha_i x_i[k], W_lo(k, own).
+    //      Warps 0, 5, 6 and 7 (four sub-partitions) each read the record with one
+    //      load per lane (lane l: word l) and share the FP64 bookkeeping:
+    //      0: pivot and f, 5: S(new), 6: FP32 copy of alpha, 7: trace (CTA 0).
+    if (warp == 0 || (warp >= 5 && warp <= 7)) {
+      const double* rw = reinterpret_cast<const double*>(mrec_at(a, par, owner_of(k, n, P)));
+      constexpr int kWords = (int)(sizeof(MixRecord) / sizeof(double));
+      static_assert(kWords <= 32, "one record word per lane");
+      const double wv = lane < kWords ? rw[lane] : 0.0;
+      auto word = [&](int i) { return __shfl_sync(0xffffffffu, wv, i); };
+      constexpr int oF = offsetof(MixRecord, f_new) / 8, oA = offsetof(MixRecord, alpha) / 8;
+      constexpr int oC = offsetof(MixRecord, coef) / 8, oT = offsetof(MixRecord, Tk) / 8;
+      const c128 al = mk(word(oA), word(oA + 1)), co = mk(word(oC), word(oC + 1));
+      const double fnew = word(oF);
+      c128 tk = mk(0.0, 0.0);  // lane p < n_o: row p of T' at pixel k
+#pragma unroll
+      for (int p = 0; p < kMaxPorts; ++p) {
+        const c128 v = mk(word(oT + 2 * p), word(oT + 2 * p + 1));
+        if (lane == p) tk = v;
       }
-    } else if (tid < 32 + r) {
-      const int i = tid - 32;
-      const float2 al = s_alpha[i], x = a.X[(size_t)k * R + i];
-      s_beta[i] = make_float2(fmaf(al.x, x.x, -al.y * x.y), fmaf(al.x, x.y, al.y * x.x));
-    } else if (tid >= 256 && tid < 256 + own) {
-      const int jl = tid - 256;
-      const c128 w = wlo_sym(a, k, pb + jl);
-      s_wk[jl] = make_float2((float)w.x, (float)w.y);
-    }
-    __syncthreads();
-    tick(2);
-    // ---- keep the flip of pixel k
-    if (!isfinite(s_f)) status = PNGF_ENUMERIC;
-    if (a.mode == PNGF_FIRST_IMPROVEMENT) {
-      n_evals += pos_k - t + 1;
-      t = pos_k + 1;
-    } else {
-      n_evals += n;
-      ++sweeps_done;
-    }
-    ++acc_in_sweep;
-    if (tid == 0) {
-      if (cta == 0) {
+      if (warp == 0) {
+        if (lane < n_o) s_pv.Tk[lane] = tk;
+        if (lane == 0) {
+          s_pv.k = k;
+          s_pv.alpha = al;
+          s_pv.coef = co;
+          s_f = fnew;
+          s_bad = !isfinite(fnew);
+        }
+      } else if (warp == 5) {
+        // S(new) exactly as the scorer formed it for its objective
+        if (lane < n_o) s_S[lane] = cfma(co, tk, s_S[lane]);
+      } else if (warp == 6) {
+        if (lane == 0) s_alpha[r] = make_float2((float)al.x, (float)al.y);
+      } else if (cta == 0 && lane == 0) {
         if (n_acc < a.trace_cap) {
           if (a.trace) {
             int32_t* tr = a.trace + 4 * n_acc;
@@ -423,14 +428,32 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
             tr[2] = k;
             tr[3] = 0;
           }
-          if (a.trace_f) a.trace_f[n_acc] = s_f;
-        } else if (status == PNGF_OK) {
-          status = PNGF_ECAPACITY;
+          if (a.trace_f) a.trace_f[n_acc] = fnew;
         }
-        a.xa[r] = s_pv.alpha;
+        a.xa[r] = al;
       }
-      s_alpha[r] = make_float2((float)s_pv.alpha.x, (float)s_pv.alpha.y);
+    } else if (tid >= 32 && tid < 32 + r) {
+      const int i = tid - 32;
+      const float2 al = s_alpha[i], x = a.X[(size_t)k * R + i];
+      s_beta[i] = make_float2(fmaf(al.x, x.x, -al.y * x.y), fmaf(al.x, x.y, al.y * x.x));
+    } else if (tid >= 256 && tid < 256 + own) {
+      const int jl = tid - 256, j = pb + jl;
+      const size_t o = (size_t)min(k, j) * a.ldl + max(k, j);  // upper triangle of the symmetric W_lo
+      s_wk[jl] = make_float2(a.Wr[o], a.Wi[o]);
     }
+    __syncthreads();
+    tick(2);
+    // ---- keep the flip of pixel k
+    if (s_bad) status = PNGF_ENUMERIC;
+    if (n_acc >= a.trace_cap && status == PNGF_OK) status = PNGF_ECAPACITY;
+    if (a.mode == PNGF_FIRST_IMPROVEMENT) {
+      n_evals += pos_k - t + 1;
+      t = pos_k + 1;
+    } else {
+      n_evals += n;
+      ++sweeps_done;
+    }
+    ++acc_in_sweep;
     ++n_acc;
     // U2: a 16-lane group per own pixel forms the delayed sum in FP32 and the
     // column entry c_j = W_lo(k, j) + sum_i beta_i x_i[j] (FP32)
@@ -496,32 +519,23 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         refresh_x(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(8);
-        // the delayed set is empty here: its shared memory holds the active-pixel list
+        // the delayed set is empty here: its shared memory holds the active-pixel
+        // list, then the staging of the correction
         const int m_act = refresh_residual(a, pb, pe, reinterpret_cast<int*>(work));
+        const int t_end = count_below(reinterpret_cast<const int*>(work), m_act, pe - 1);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(9);
-        (void)m_act;
-        correct_tiles(a, reinterpret_cast<float*>(work));
-        tick(14);
-        if (!grid_sync(ctl)) { failed = true; break; }
-        tick(15);
-        correct_finish(a, pb, pe);
+        correct_strips<true>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(work),
+                             (int)(dynamic_smem_bytes() - kOwnStateSmem));
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(10);
         ports_partial(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(11);
         load_et();
-        if (tid == 0) {
-          c128 o[kMaxPorts];
-          FOR_PORTS(p, n_o) {
-            c128 acc = mk(0.0, 0.0);
-            for (int q = 0; q < P; ++q) acc = cadd(acc, a.opart[(size_t)q * n_o + p]);
-            o[p] = cadd(a.co[p], acc);
-            s_S[p] = cmul(csub(o[p], s_op.off[p]), s_op.scale[p]);
-          }
-          s_f = objective_of(s_op, o);
-        }
+        ports_total(a, s_o);
+        if (tid < n_o) s_S[tid] = cmul(csub(s_o[tid], s_op.off[tid]), s_op.scale[tid]);
+        if (tid == 32) s_f = objective_of(s_op, s_o);
         __syncthreads();
         tick(5);
       }
@@ -658,18 +672,26 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
 constexpr size_t kMixedWork = kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM;
 static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
 static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
-static_assert(kMixedWork >= ct_smem_bytes(1 + kMaxPorts), "tile stage of the refresh correction");
+static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
 constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
+
+static void* mixed_kernel_for(int objective) {
+  return objective == PNGF_OBJ_MAX_WEIGHTED_POWER ? (void*)dbs_mixed_kernel<PNGF_OBJ_MAX_WEIGHTED_POWER>
+                                                  : (void*)dbs_mixed_kernel<PNGF_OBJ_MIN_INSERTION_LOSS>;
+}
 
 static int mixed_grid(pngf_ctx* c) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(dbs_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedSmem);
+    cudaFuncSetAttribute(dbs_mixed_kernel<PNGF_OBJ_MAX_WEIGHTED_POWER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kMixedSmem);
+    cudaFuncSetAttribute(dbs_mixed_kernel<PNGF_OBJ_MIN_INSERTION_LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kMixedSmem);
     cudaFuncSetAttribute(flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
     attr = true;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_mixed_kernel, kThreads, kMixedSmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel_for(c->cfg.objective), kThreads, kMixedSmem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 2) per_sm = 2;
   int g = c->n_sm * per_sm;
@@ -695,7 +717,7 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   err = cudaMemsetAsync(a.slots, 0, (size_t)2 * grid * kSlotStride * sizeof(unsigned long long), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
   void* params[] = {&a};
-  err = cudaLaunchCooperativeKernel((const void*)dbs_mixed_kernel, dim3(grid), dim3(kThreads), params, kMixedSmem,
+  err = cudaLaunchCooperativeKernel(mixed_kernel_for(c->cfg.objective), dim3(grid), dim3(kThreads), params, kMixedSmem,
                                     c->stream);
   return cuda_status(err);
 }
