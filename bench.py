@@ -1,8 +1,10 @@
 """Benchmark of the PNGF direct-binary-search hot path on GB300.
 
-One step = restore the factored start state (device copies inside the
-workspace) + one complete DBS run on the device (first improvement, raster
-order, until a sweep keeps no flip or ``--sweeps`` sweeps ran).  The metric is
+One step = for each of ``--runs`` independent random starts (default 4):
+restore the factored start state (device copies inside the workspace) + one
+complete DBS run on the device (first improvement, raster order, until a
+sweep keeps no flip or ``--sweeps`` sweeps ran); the runs' persistent launches
+execute side by side, each on its own stream and share of the SMs.  The metric is
 attempted pixel flips per second in sequential DBS semantics (the paper's
 Table 1 counting: every visited flip is one evaluation).  The factorisation of
 M is timed separately (``factor_ms``), as the paper reports the initial
@@ -45,6 +47,8 @@ def parse():
                     help="mixed path: fold the delayed set with tcgen05 (1) or FP32 CUDA cores (0)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--sweeps", type=int, default=10)
+    ap.add_argument("--runs", type=int, default=4,
+                    help="independent runs per GPU (random starts), launched side by side on their own streams")
     ap.add_argument("--refresh-k", type=int, default=64)
     ap.add_argument("--tau", type=float, default=1e-9)
     ap.add_argument("--cpu-sample-evals", type=int, default=16)
@@ -321,6 +325,83 @@ def bench_batch(args, torch, dist, dev, P, Wl):
 
 
 # ---------------------------------------------------------------- GPU arm
+class RunSet:
+    """B independent DBS runs (seeds seed0 .. seed0 + B - 1) on one device, each
+    with its own context, stream and persistent grid of ctas CTAs; a step forks
+    from the timing stream, runs restore + pngf_dbs_sweep on every run's stream
+    (the cooperative launches execute side by side) and joins back."""
+
+    def __init__(self, torch, P, Wl, case, dev, precision, args, seeds, ctas, tstream, inputs=None):
+        self.torch, self.P, self.case, self.dev, self.tstream = torch, P, case, dev, tstream
+        self.n = case.n_d
+        self.sweeps = args.sweeps
+        self.trace_cap = args.sweeps * self.n
+        self.streams = [torch.cuda.Stream(dev) for _ in seeds]
+        self.ctxs, self.traces, self.trace_f, self.counters = [], [], [], []
+        self.factor_ms = []
+        for i, seed in enumerate(seeds):
+            s = self.streams[i]
+            with torch.cuda.stream(s):
+                kw = dict(precision=precision, tau=args.tau, refresh_k=args.refresh_k, device=str(dev), stream=s,
+                          n_ctas=ctas)
+                if precision == P.PNGF_MIXED:
+                    kw.update(delay_r=args.delay_r, tensor_fold=args.tensor_fold)
+                if inputs is not None:
+                    kw["inputs_on_device"] = inputs
+                c = P.DbsContext(case, **kw)
+                if inputs is None:
+                    inputs = (c.G, c.God, c.cd, c.co, c.dv)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                c.factor(Wl.random_design(self.n, seed=seed))
+                e1.record(s)
+                s.synchronize()
+                self.factor_ms.append(e0.elapsed_time(e1))
+                if c.sync() != 0:
+                    raise P.PngfError(c.sync(), "pngf_factor")
+                c.snapshot()
+                self.ctxs.append(c)
+                self.traces.append(torch.zeros((self.trace_cap, 4), dtype=torch.int32, device=dev))
+                self.trace_f.append(torch.zeros(self.trace_cap, dtype=torch.float64, device=dev))
+                self.counters.append(torch.zeros(8, dtype=torch.int64, device=dev))
+        self.inputs = inputs
+        self.kev = None
+
+    def step(self, i_step=None, orders=None):
+        torch, P = self.torch, self.P
+        fork = torch.cuda.Event()
+        fork.record(self.tstream)
+        joins = []
+        for r, (c, s) in enumerate(zip(self.ctxs, self.streams)):
+            s.wait_event(fork)
+            P.pngf_restore(c.ctx)
+            if i_step is not None:
+                self.kev[i_step][r][0].record(s)
+            P.pngf_dbs_sweep(c.ctx, self.sweeps, None if orders is None else orders[r], self.traces[r].data_ptr(),
+                             self.trace_f[r].data_ptr(), self.trace_cap, self.counters[r].data_ptr())
+            if i_step is not None:
+                self.kev[i_step][r][1].record(s)
+            j = torch.cuda.Event()
+            j.record(s)
+            joins.append(j)
+        for j in joins:
+            self.tstream.wait_event(j)
+
+    def arm_events(self, steps):
+        ev = self.torch.cuda.Event
+        self.kev = [[(ev(enable_timing=True), ev(enable_timing=True)) for _ in self.ctxs] for _ in range(steps)]
+
+    def counts(self):
+        return np.stack([c.cpu().numpy() for c in self.counters])
+
+    def status(self):
+        return [c.sync() for c in self.ctxs]
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -344,224 +425,216 @@ def main():
     case = Wl.get_case(case_name(args.workload))
     n, n_o = case.n_d, case.n_o
     prec = P.PNGF_MIXED if args.precision == "mixed" else P.PNGF_FP64
-    stream = torch.cuda.Stream(dev)
-    with torch.cuda.stream(stream):
-        ctx = P.DbsContext(case, precision=prec, tau=args.tau, refresh_k=args.refresh_k, delay_r=args.delay_r,
-                           device=str(dev), stream=stream, tensor_fold=args.tensor_fold)
-        b0 = Wl.random_design(n, seed=dist.rank)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.factor(b0)
-        e1.record(stream)
-        stream.synchronize()
-        factor_ms = e0.elapsed_time(e1)
-        st = ctx.sync()
-        if st != 0:
-            raise P.PngfError(st, "pngf_factor")
-        ctx.snapshot()
-        trace_cap = args.sweeps * n
-        trace = torch.zeros((trace_cap, 4), dtype=torch.int32, device=dev)
-        trace_f = torch.zeros(trace_cap, dtype=torch.float64, device=dev)
-        counters = torch.zeros(8, dtype=torch.int64, device=dev)
-        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-
-        def step(i=None, order_ptr=None):
-            P.pngf_restore(ctx.ctx)
-            if i is not None:
-                kev[i][0].record(stream)
-            P.pngf_dbs_sweep(ctx.ctx, args.sweeps, order_ptr, trace.data_ptr(), trace_f.data_ptr(), trace_cap,
-                             counters.data_ptr())
-            if i is not None:
-                kev[i][1].record(stream)
-
-        for _ in range(max(args.warmup, 1)):
-            step()
-        stream.synchronize()
-        st = ctx.sync()
-        if st not in (0,):
-            raise P.PngfError(st, "warm-up")
-        c = counters.cpu().numpy().copy()
-        evals_per_step, acc_per_step, sweeps_per_step = int(c[1]), int(c[0]), int(c[2])
-        peak_fp64 = fp64_peak_gflops(stream.cuda_stream)
-        # ---- timed region (device time, CUDA events on the launching stream)
-        dist.barrier()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    n_runs = max(1, args.runs)
+    ctas = 0 if n_runs == 1 else nsm // n_runs
+    seeds = [dist.rank * n_runs + i for i in range(n_runs)]
+    tstream = torch.cuda.Stream(dev)
+    rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream)
+    for _ in range(max(args.warmup, 1)):
+        rs.step()
+    torch.cuda.synchronize(dev)
+    st = rs.status()
+    if any(s != 0 for s in st):
+        raise P.PngfError(max(st), "warm-up")
+    c = rs.counts()
+    evals_per_step, acc_per_step, sweeps_per_step = int(c[:, 1].sum()), int(c[:, 0].sum()), int(c[:, 2].sum())
+    peak_fp64 = fp64_peak_gflops(tstream.cuda_stream)
+    # ---- timed region (device time, CUDA events on the timing stream that forks and joins every run)
+    rs.arm_events(args.steps)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(tstream)
+    for i in range(args.steps):
+        rs.step(i)
+    t1.record(tstream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    dist.barrier()
+    st = rs.status()
+    if any(s != 0 for s in st):
+        raise P.PngfError(max(st), "timed steps")
+    c2 = rs.counts()
+    assert int(c2[:, 1].sum()) == evals_per_step, "steps are not identical runs"
+    cyc = rs.ctxs[0].phase_cycles()
+    mhz = clk.get("sm_mhz") or 2070.0
+    phase_names = ["score", "wait_after_score", "select_pivot_gather", "wait_or_flush",
+                   "update", "refresh", "sweep_setup", "kernel_total", "refresh_x", "refresh_residual",
+                   "refresh_correct", "refresh_ports", "publish", "update_delayed_sum",
+                   "fold_prepare", "unused15"]
+    phase_ms = {nm: float(cv) / (mhz * 1e3) for nm, cv in zip(phase_names, cyc)}
+    ms = t0.elapsed_time(t1)
+    ms_max = dist.max(torch, ms, dev)
+    total_evals = dist.sum(torch, float(evals_per_step * args.steps), dev)
+    value = total_evals / (ms_max / 1e3)
+    kms = [a.elapsed_time(b) for per_step in rs.kev for a, b in per_step]
+    k_avg = sum(kms) / len(kms)
+    step_ms = ms / args.steps
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tri = n * (n + 1) / 2
+    runs_note = ("%d concurrent cooperative launches (one per run, %d CTAs each): achieved = the launches' "
+                 "algorithmic work per step / device time of a step" % (n_runs, ctas)) if n_runs > 1 else None
+    if prec == P.PNGF_FP64:
+        # dominant kernel: the persistent FP64 DBS sweep.  Algorithmic work per
+        # launch: the rank-1 update of the upper triangle of W per kept flip,
+        # 4 DFMA = 8 flop per complex element (32 bytes of W read + written).
+        flops = acc_per_step * 8.0 * tri
+        bytes_w = acc_per_step * 32.0 * tri
+        achieved_gflops = flops / (step_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved_gflops / 1e3, "peak": peak_fp64 / 1e3,
+                    "unit": "TFLOP/s", "frac": achieved_gflops / peak_fp64, "traffic": None,
+                    "kernel": "dbs_fp64_kernel",
+                    "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks "
+                                   "(152 SMs x 2 DFMA/clk x 2 flop x clock)",
+                    "hbm_view": {"achieved_gbs": bytes_w / (step_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                                 "frac": bytes_w / (step_ms / 1e3) / 1e9 / hbm_peak,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
+    else:
+        # dominant kernel: the persistent mixed DBS sweep.  Algorithmic HBM bytes per
+        # launch: per flush the upper triangle of the two FP32 planes read + written
+        # (16 B per element), per refresh one read of G (16 B) and of the FP32
+        # upper triangle (8 B), per kept flip one column of the FP32 planes (8 B x n),
+        # per evaluation (3 + n_o) x 16 B of FP64 state.
+        n_flush, n_ref = int(c2[:, 5].sum()), int(c2[:, 4].sum())
+        bytes_alg = (n_flush * 16.0 * tri + n_ref * (16.0 * n * n + 8.0 * tri) + acc_per_step * 8.0 * n
+                     + evals_per_step * (3 + n_o) * 16.0)
+        gbs = bytes_alg / (step_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "traffic": None, "kernel": "dbs_mixed_kernel",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
+                    "note": "each run keeps one flip at a time (a latency-bound chain of word exchange, "
+                            "fetch and FP64 state update per kept flip) and refreshes e, T in FP64 (FP64-pipe "
+                            "bound); see phase_ms_cta0"}
+    if runs_note:
+        roofline["runs"] = runs_note
+    # ---- end to end through the C ABI with host buffers (pinned): visiting orders in,
+    #      traces, objective values, counters and port amplitudes out, every step
+    e2e = None
+    if not args.no_e2e:
+        order_h = torch.from_numpy(np.tile(np.arange(n, dtype=np.int32), (args.sweeps, 1))).pin_memory()
+        orders_d = [torch.empty_like(order_h, device=dev) for _ in rs.ctxs]
+        outs = [(torch.empty((rs.trace_cap, 4), dtype=torch.int32).pin_memory(),
+                 torch.empty(rs.trace_cap, dtype=torch.float64).pin_memory(),
+                 torch.empty(8, dtype=torch.int64).pin_memory()) for _ in rs.ctxs]
+        h2d = order_h.numel() * 4 * n_runs
+        d2h = (outs[0][0].numel() * 4 + outs[0][1].numel() * 8 + 64 + 16 * n_o + 8) * n_runs
+        for rep in range(2):
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            for i in range(args.steps):
+                for r, s in enumerate(rs.streams):
+                    with torch.cuda.stream(s):
+                        orders_d[r].copy_(order_h, non_blocking=True)
+                for r, s in enumerate(rs.streams):  # the step forks after every run's copy
+                    ev = torch.cuda.Event()
+                    ev.record(s)
+                    tstream.wait_event(ev)
+                rs.step(None, [o.data_ptr() for o in orders_d])
+                for r, s in enumerate(rs.streams):
+                    with torch.cuda.stream(s):
+                        outs[r][0].copy_(rs.traces[r], non_blocking=True)
+                        outs[r][1].copy_(rs.trace_f[r], non_blocking=True)
+                        outs[r][2].copy_(rs.counters[r], non_blocking=True)
+                for cx in rs.ctxs:
+                    cx.eval_ports()  # synchronizes: each run's result on the host
+            w1 = time.perf_counter()
+        assert sum(int(o[2][1]) for o in outs) == evals_per_step
+        e2e_s = dist.max(torch, w1 - w0, dev)
+        e2e = {"value": total_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    # ---- the same runs on the FP64 path (same GPU, same starts, same concurrency)
+    #      for the speedup and the S-parameter error of the mixed path
+    rs.step()
+    torch.cuda.synchronize(dev)
+    res_main = [(cx.eval_ports()[0], cx.design(), rs.traces[r][:min(int(c2[r, 0]), rs.trace_cap), 2].cpu().numpy())
+                for r, cx in enumerate(rs.ctxs)]
+    compare = None
+    if prec == P.PNGF_MIXED and not args.no_fp64_compare:
+        ref = RunSet(torch, P, Wl, case, dev, P.PNGF_FP64, args, seeds, ctas, tstream, inputs=rs.inputs)
+        ref.step()
         torch.cuda.synchronize(dev)
-        clocks = Clocks(dist.local)
-        clocks.start()
-        time.sleep(0.3)
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for i in range(args.steps):
-            step(i)
-        t1.record(stream)
-        stream.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        r0.record(tstream)
+        for _ in range(reps):
+            ref.step()
+        r1.record(tstream)
         torch.cuda.synchronize(dev)
-        clk = clocks.stop()
-        dist.barrier()
-        st = ctx.sync()
-        if st != 0:
-            raise P.PngfError(st, "timed steps")
-        c2 = counters.cpu().numpy()
-        assert int(c2[1]) == evals_per_step, "steps are not identical runs"
-        cyc = ctx.phase_cycles()
-        mhz = clk.get("sm_mhz") or 2070.0
-        phase_names = ["score", "wait_after_score", "select_pivot_gather", "wait_or_flush",
-                       "update", "refresh", "sweep_setup", "kernel_total", "refresh_x", "refresh_residual",
-                       "refresh_correct", "refresh_ports", "publish", "update_delayed_sum",
-                       "unused14", "unused15"]
-        phase_ms = {nm: float(cv) / (mhz * 1e3) for nm, cv in zip(phase_names, cyc)}
-        ms = t0.elapsed_time(t1)
-        ms_max = dist.max(torch, ms, dev)
-        total_evals = dist.sum(torch, float(evals_per_step * args.steps), dev)
-        value = total_evals / (ms_max / 1e3)
-        kms = [a.elapsed_time(b) for a, b in kev]
-        k_avg = sum(kms) / len(kms)
-        peaks = measured_peaks()
-        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-        tri = n * (n + 1) / 2
-        if prec == P.PNGF_FP64:
-            # dominant kernel: the persistent FP64 DBS sweep.  Algorithmic work per
-            # launch: the rank-1 update of the upper triangle of W per kept flip,
-            # 4 DFMA = 8 flop per complex element (32 bytes of W read + written).
-            flops = acc_per_step * 8.0 * tri
-            bytes_w = acc_per_step * 32.0 * tri
-            achieved_gflops = flops / (k_avg / 1e3) / 1e9
-            roofline = {"bound": "alu", "achieved": achieved_gflops / 1e3, "peak": peak_fp64 / 1e3,
-                        "unit": "TFLOP/s", "frac": achieved_gflops / peak_fp64, "traffic": None,
-                        "kernel": "dbs_fp64_kernel",
-                        "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks "
-                                       "(152 SMs x 2 DFMA/clk x 2 flop x clock)",
-                        "hbm_view": {"achieved_gbs": bytes_w / (k_avg / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                                     "frac": bytes_w / (k_avg / 1e3) / 1e9 / hbm_peak,
-                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
-        else:
-            # dominant kernel: the persistent mixed DBS sweep.  Algorithmic HBM bytes per
-            # launch: per flush the upper triangle of the two FP32 planes read + written
-            # (16 B per element), per refresh one read of G (16 B) and of the FP32
-            # upper triangle (8 B), per kept flip one column of the FP32 planes (8 B x n),
-            # per evaluation (3 + n_o) x 16 B of FP64 state.
-            n_flush, n_ref = int(c2[5]), int(c2[4])
-            bytes_alg = (n_flush * 16.0 * tri + n_ref * (16.0 * n * n + 8.0 * tri) + acc_per_step * 8.0 * n
-                         + evals_per_step * (3 + n_o) * 16.0)
-            gbs = bytes_alg / (k_avg / 1e3) / 1e9
-            roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                        "traffic": None, "kernel": "dbs_mixed_kernel",
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
-                        "note": "one kept flip at a time: the single-run search is latency-bound "
-                                "(grid barrier + selection per kept flip); see phase_ms_cta0"}
-        # ---- end to end through the C ABI with host buffers
-        e2e = None
-        if not args.no_e2e:
-            order_h = torch.from_numpy(np.tile(np.arange(n, dtype=np.int32), (args.sweeps, 1))).pin_memory()
-            order_d = torch.empty_like(order_h, device=dev)
-            trace_h = torch.empty((trace_cap, 4), dtype=torch.int32).pin_memory()
-            trace_fh = torch.empty(trace_cap, dtype=torch.float64).pin_memory()
-            cnt_h = torch.empty(8, dtype=torch.int64).pin_memory()
-            h2d = order_h.numel() * 4
-            d2h = trace_h.numel() * 4 + trace_fh.numel() * 8 + cnt_h.numel() * 8 + 16 * n_o + 8
-            for rep in range(2):
-                dist.barrier()
-                torch.cuda.synchronize(dev)
-                w0 = time.perf_counter()
-                for i in range(args.steps):
-                    order_d.copy_(order_h, non_blocking=True)
-                    step(None, order_d.data_ptr())
-                    trace_h.copy_(trace, non_blocking=True)
-                    trace_fh.copy_(trace_f, non_blocking=True)
-                    cnt_h.copy_(counters, non_blocking=True)
-                    o_host, f_host = ctx.eval_ports()  # synchronizes: the step's result on the host
-                w1 = time.perf_counter()
-            assert int(cnt_h[1]) == evals_per_step
-            e2e_s = dist.max(torch, w1 - w0, dev)
-            e2e = {"value": total_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)}
-        # ---- the same run on the FP64 path (same GPU, same start) for the speedup and
-        #      the S-parameter error of the mixed path
-        compare = None
-        restore_and_run = step
-        restore_and_run()
-        stream.synchronize()
-        o_main, f_main = ctx.eval_ports()
-        b_main = ctx.design()
-        trace_main = trace[:min(acc_per_step, trace_cap), 2].cpu().numpy().copy()
-        if prec == P.PNGF_MIXED and not args.no_fp64_compare:
-            ref = P.DbsContext(case, precision=P.PNGF_FP64, tau=args.tau, refresh_k=args.refresh_k, device=str(dev),
-                               stream=stream, inputs_on_device=(ctx.G, ctx.God, ctx.cd, ctx.co, ctx.dv))
-            ref.factor(b0)
-            ref.snapshot()
-            cnt64 = torch.zeros(8, dtype=torch.int64, device=dev)
-            tr64 = torch.zeros((trace_cap, 4), dtype=torch.int32, device=dev)
-
-            def step64():
-                P.pngf_restore(ref.ctx)
-                P.pngf_dbs_sweep(ref.ctx, args.sweeps, None, tr64.data_ptr(), None, trace_cap, cnt64.data_ptr())
-
-            step64()
-            stream.synchronize()
-            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 2
-            r0.record(stream)
-            for _ in range(reps):
-                step64()
-            r1.record(stream)
-            stream.synchronize()
-            if ref.sync() != 0:
-                raise RuntimeError("FP64 comparison run failed")
-            c64 = cnt64.cpu().numpy()
-            ms64 = r0.elapsed_time(r1) / reps
-            o64, f64 = ref.eval_ports()
-            b64 = ref.design()
-            k64 = tr64[:min(int(c64[0]), trace_cap), 2].cpu().numpy()
-            same = bool(np.array_equal(b64, b_main))
-            prefix = next((i for i, (x, y) in enumerate(zip(k64, trace_main)) if x != y), min(len(k64), len(trace_main)))
-            S_main = (o_main - case.s_off) * case.s_scale
-            S_64 = (o64 - case.s_off) * case.s_scale
-            compare = {"fp64_evals_per_s": float(c64[1]) / (ms64 / 1e3), "fp64_ms_per_step": ms64,
-                       "speedup_vs_fp64": (float(c64[1]) / (ms64 / 1e3)) and value / (float(c64[1]) / (ms64 / 1e3)),
-                       "same_final_design": same, "identical_accept_prefix": int(prefix),
-                       "accepts_fp64": int(c64[0]), "accepts_mixed": int(acc_per_step)}
+        if any(s != 0 for s in ref.status()):
+            raise RuntimeError("FP64 comparison runs failed")
+        c64 = ref.counts()
+        ms64 = r0.elapsed_time(r1) / reps
+        ev64 = float(c64[:, 1].sum()) / (ms64 / 1e3)
+        same_all, prefix_min, s_err = True, None, 0.0
+        for r, cx in enumerate(ref.ctxs):
+            o64 = cx.eval_ports()[0]
+            b64 = cx.design()
+            k64 = ref.traces[r][:min(int(c64[r, 0]), ref.trace_cap), 2].cpu().numpy()
+            o_m, b_m, k_m = res_main[r]
+            same = bool(np.array_equal(b64, b_m))
+            same_all = same_all and same
+            prefix = next((i for i, (x, y) in enumerate(zip(k64, k_m)) if x != y), min(len(k64), len(k_m)))
+            prefix_min = prefix if prefix_min is None else min(prefix_min, prefix)
             if same:
-                compare["s_param_max_rel_err_vs_fp64"] = float(
-                    np.max(np.abs(S_main - S_64) / np.maximum(np.abs(S_64), 1e-3)))
-            ref.close()
-        if dist.rank == 0:
-            import oracle as O
-            ev = O.evaluate(O.Problem.from_case(case), b_main)
+                S_m = (o_m - case.s_off) * case.s_scale
+                S_64 = (o64 - case.s_off) * case.s_scale
+                s_err = max(s_err, float(np.max(np.abs(S_m - S_64) / np.maximum(np.abs(S_64), 1e-3))))
+        compare = {"fp64_evals_per_s": ev64, "fp64_ms_per_step": ms64, "speedup_vs_fp64": value / ev64,
+                   "same_final_design": same_all, "identical_accept_prefix_min": int(prefix_min),
+                   "accepts_fp64": int(c64[:, 0].sum()), "accepts_mixed": int(acc_per_step),
+                   "runs_compared": n_runs}
+        if same_all:
+            compare["s_param_max_rel_err_vs_fp64"] = s_err
+        ref.close()
+    if dist.rank == 0:
+        import oracle as O
+        p = O.Problem.from_case(case)
+        err = 0.0
+        for o_m, b_m, _ in res_main:
+            ev = O.evaluate(p, b_m)
             S_exact = (ev.o - case.s_off) * case.s_scale
-            S_main = (o_main - case.s_off) * case.s_scale
-            compare = dict(compare or {})
-            compare["s_param_max_rel_err_vs_oracle"] = float(
-                np.max(np.abs(S_main - S_exact) / np.maximum(np.abs(S_exact), 1e-3)))
-            compare["s_param_err_note"] = "final design of the timed run, exact S from the CPU FP64 oracle"
-        cpu = None
-        if dist.rank == 0 and not args.no_cpu_baseline:
-            v, m, dt = time_oracle(case, b0, args.cpu_sample_evals)
-            cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                   "sample": f"first {m} attempted flips of the same raster DBS run, each re-solved with "
-                             f"LAPACK zgesv at n={n} ({dt:.1f} s)"}
+            S_m = (o_m - case.s_off) * case.s_scale
+            err = max(err, float(np.max(np.abs(S_m - S_exact) / np.maximum(np.abs(S_exact), 1e-3))))
+        compare = dict(compare or {})
+        compare["s_param_max_rel_err_vs_oracle"] = err
+        compare["s_param_err_note"] = ("final design of every timed run, exact S from the CPU FP64 oracle "
+                                       "(relative to max(|S|, 1e-3))")
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        v, m, dt = time_oracle(case, Wl.random_design(n, seed=seeds[0]), args.cpu_sample_evals)
+        cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"first {m} attempted flips of the same raster DBS run, each re-solved with "
+                         f"LAPACK zgesv at n={n} ({dt:.1f} s)"}
     if dist.rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=dist.world, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f64" if prec == P.PNGF_FP64 else "f32+f64", data="synthetic",
             config={"workload": args.workload, "n_d": n, "n_o": n_o, "precision": args.precision,
+                    "runs_per_gpu": n_runs, "ctas_per_run": ctas if ctas else nsm,
+                    "seeds": seeds,
                     "mode": "first-improvement, raster order", "max_sweeps": args.sweeps,
                     "refresh_k": args.refresh_k, "tau": args.tau,
                     "delay_r": args.delay_r if prec == P.PNGF_MIXED else None,
                     "fold": ("tcgen05 3xTF32" if args.tensor_fold else "FP32 CUDA cores")
                     if prec == P.PNGF_MIXED else None,
-                    "step": "restore factored start state + DBS run to convergence",
-                    "l2": "inputs larger than L2 (W = %.0f MB complex128)" % (n * n * 16 / 1e6),
-                    "replicas": "one independent run per GPU (seed = rank)"},
-            roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk, gpu_launches=args.steps,
+                    "step": "restore every run's factored start state + DBS to convergence, runs concurrent",
+                    "l2": "inputs larger than L2 (W = %.0f MB complex128 per run)" % (n * n * 16 / 1e6),
+                    "replicas": "independent runs per GPU (seed = rank * runs + i)"},
+            roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk, gpu_launches=args.steps * n_runs,
             evals_per_step=evals_per_step, accepts_per_step=acc_per_step, sweeps_per_step=sweeps_per_step,
             accepts_per_s=acc_per_step * args.steps / (ms_max / 1e3),
             sweeps_per_s=sweeps_per_step * args.steps / (ms_max / 1e3),
-            kernel_ms_avg=k_avg, factor_ms=factor_ms, fp64_peak_gflops=peak_fp64, phase_ms_cta0=phase_ms,
-            mixed_vs_fp64=compare)
+            kernel_ms_avg=k_avg, factor_ms=statistics.mean(rs.factor_ms), fp64_peak_gflops=peak_fp64,
+            phase_ms_cta0=phase_ms, mixed_vs_fp64=compare)
         print(json.dumps(line))
-    ctx.close()
+    rs.close()
     return 0
 
 

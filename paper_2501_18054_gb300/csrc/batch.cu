@@ -71,22 +71,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   __shared__ int s_k;
   __shared__ long long s_best;
   // tensor-core fold: this CTA holds TC_TMEM_COLS columns of tensor memory for all its runs
-  __shared__ __align__(8) unsigned long long s_mb_load, s_mb_mma;
+  __shared__ __align__(8) unsigned long long s_tc_bars[4];
   __shared__ unsigned s_tmem;
   const bool use_tc = n_runs > 0 && runs[0].tensor_fold;
-  TcState tcs;
-  tcs.tmem = 0;
-  tcs.ph_load = tcs.ph_mma = 0;
-  if (use_tc) {
-    tc_mbar_init(&s_mb_load, &s_mb_mma);
-    tc_alloc(&s_tmem);
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    tcs.tmem = s_tmem;
-    tcs.mb_load = (unsigned)__cvta_generic_to_shared(&s_mb_load);
-    tcs.mb_mma = (unsigned)__cvta_generic_to_shared(&s_mb_mma);
-  }
+  TcState tcs{};
+  if (use_tc) tc_setup(tcs, s_tc_bars, &s_tmem);
   bool tc_failed = false;
   for (int run = blockIdx.x; run < n_runs && !tc_failed; run += gridDim.x) {
     const SweepArgs& a = runs[run];
@@ -296,15 +285,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
       if (status == PNGF_ENUMERIC || status == PNGF_EINVAL || status == PNGF_ETIMEOUT) latch_status(ctl, status);
     }
   }
-  if (use_tc) {
-    if (tc_failed && threadIdx.x < 128) {
-      mbar_wait(tcs.mb_load, tcs.ph_load);
-      mbar_wait(tcs.mb_mma, tcs.ph_mma);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    tc_free(tcs.tmem);
-  }
+  if (use_tc) tc_teardown(tcs, tc_failed);
 }
 
 }  // namespace

@@ -1,5 +1,5 @@
 // Stand-alone launches of the tensor-core fold (see flush_tc.cuh): a prepare
-// pass over the whole grid, then a tile pass of 128-thread CTAs that each own
+// pass over the whole grid, then a tile pass of 256-thread CTAs that each own
 // 128 tensor-memory columns.  Used by the single-call accept path when the
 // delayed set is full; the persistent search runs the same device code.
 #include "flush_tc.cuh"
@@ -13,35 +13,18 @@ __global__ void flush_tc_prepare_kernel(SweepArgs a, unsigned char* imgA, unsign
   tc_prepare(a, r, imgA, imgB, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(128) flush_tc_kernel(SweepArgs a, const unsigned char* imgA,
+__global__ void __launch_bounds__(256, 2) flush_tc_kernel(SweepArgs a, const unsigned char* imgA,
                                                        const unsigned char* imgB) {
   extern __shared__ __align__(128) unsigned char tc_dyn[];
-  __shared__ __align__(8) unsigned long long mb_load, mb_mma;
+  __shared__ __align__(8) unsigned long long bars[4];
   __shared__ unsigned tmem_slot;
   const int r = a.ctl->r_delay;
   if (r < a.R) return;
-  tc_mbar_init(&mb_load, &mb_mma);
-  tc_alloc(&tmem_slot);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  TcState st;
-  st.tmem = tmem_slot;
-  st.mb_load = (unsigned)__cvta_generic_to_shared(&mb_load);
-  st.mb_mma = (unsigned)__cvta_generic_to_shared(&mb_mma);
-  st.ph_load = st.ph_mma = 0;
-  bool ok = tc_fold_tiles(a, r, imgA, imgB, tc_dyn, st, blockIdx.x, gridDim.x);
-  if (!ok) {
-    if (threadIdx.x == 0) latch_status(a.ctl, PNGF_ETIMEOUT);
-    // give whatever is still in flight a bounded time to land before the free
-    if (threadIdx.x < 128) {
-      mbar_wait(st.mb_load, st.ph_load);
-      mbar_wait(st.mb_mma, st.ph_mma);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  tc_free(st.tmem);
+  TcState st{};
+  tc_setup(st, bars, &tmem_slot);
+  const bool ok = tc_fold_tiles(a, r, imgA, imgB, tc_dyn, st, blockIdx.x, gridDim.x);
+  if (!ok && threadIdx.x == 0) latch_status(a.ctl, PNGF_ETIMEOUT);
+  tc_teardown(st, !ok);  // after a failure: bounded wait for what was issued
 }
 
 }  // namespace
@@ -57,7 +40,7 @@ pngf_status flush_tc_launch(pngf_ctx* c) {
     attr = true;
   }
   flush_tc_prepare_kernel<<<c->n_sm * 4, 256, 0, c->stream>>>(a, imgA, imgB);
-  flush_tc_kernel<<<c->n_sm * 2, 128, TC_SMEM, c->stream>>>(a, imgA, imgB);
+  flush_tc_kernel<<<c->n_sm * 2, 256, TC_SMEM, c->stream>>>(a, imgA, imgB);
   return cuda_status(cudaGetLastError());
 }
 

@@ -14,14 +14,16 @@
 //      images laid out exactly as the shared-memory tiles (K-major, no
 //      swizzle: 8-row x 16-byte core matrices, 128 B apart along K, 1024 B
 //      apart along the rows);
-//   2. per K-chunk of 32, one bulk asynchronous copy (cp.async.bulk, the TMA
-//      engine) per operand brings the images into shared memory, completing
-//      an mbarrier transaction count;
+//   2. per K-chunk of 16, one bulk asynchronous copy (cp.async.bulk, the TMA
+//      engine) per operand brings the images into one of two shared-memory
+//      buffers, completing that buffer's mbarrier transaction count; the copy
+//      of chunk c + 1 runs while the tensor cores work on chunk c;
 //   3. one thread issues tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8)
-//      into two 64-column accumulators in tensor memory and commits to an
-//      mbarrier;
-//   4. the four warps read the accumulators back with tcgen05.ld, stage them
-//      in shared memory and add them into W_lo with coalesced accesses.
+//      into two 64-column accumulators in tensor memory and commits to the
+//      buffer's MMA mbarrier;
+//   4. the tile of W_lo is read into registers when the tile starts; four
+//      warps read the accumulators back with tcgen05.ld and stage them in
+//      shared memory, and every thread adds them into its part of the tile.
 // Every wait is bounded: on expiry the CTA latches PNGF_ETIMEOUT, waits
 // (bounded) for what it issued, frees its tensor memory and returns.
 #pragma once
@@ -33,18 +35,22 @@ namespace {
 
 constexpr int TC_M = 128;            // rows of an output tile (MMA M)
 constexpr int TC_N = 64;             // columns of an output tile (MMA N)
-constexpr int TC_KC = 32;            // delayed columns per K-chunk
+constexpr int TC_KC = 16;            // delayed columns per K-chunk
 constexpr int TC_ASUB = TC_M * TC_KC * 4;  // one A sub-image (hi or lo, re or im): 16 KB
 constexpr int TC_BSUB = TC_N * TC_KC * 4;  // one B sub-image: 8 KB
 constexpr int TC_ACHUNK = 4 * TC_ASUB;     // Yr_hi, Yr_lo, Yi_hi, Yi_lo
 constexpr int TC_BCHUNK = 4 * TC_BSUB;     // Xr_hi, Xr_lo, Xi_hi, Xi_lo
-constexpr int TC_SMEM = TC_ACHUNK + TC_BCHUNK;  // 96 KB
+constexpr int TC_BUF = TC_ACHUNK + TC_BCHUNK;   // one buffer: 48 KB
+constexpr int TC_SMEM = 2 * TC_BUF;             // two buffers: 96 KB
 constexpr int TC_TMEM_COLS = 128;               // Dr: columns 0..63, Di: 64..127
 constexpr unsigned long long kTcSpin = 1ull << 22;
 
-// byte offset of element (row, k) inside a K-major no-swizzle image of 32 K
+// byte offset of element (row, k) inside a K-major no-swizzle image of TC_KC
+// columns: 8-row x 16-byte core matrices, 128 B apart along K, TC_SBO apart
+// along the rows
+constexpr int TC_SBO = TC_KC / 4 * 128;
 __host__ __device__ __forceinline__ int tc_off(int row, int k) {
-  return (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+  return (row >> 3) * TC_SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -54,12 +60,12 @@ __device__ __forceinline__ float tf32_hi(float x) {
 }
 
 // shared-memory matrix descriptor (K-major, no swizzle): start, LBO = 128 B
-// between core matrices along K, SBO = 1024 B between 8-row groups, version 1
+// between core matrices along K, SBO = TC_SBO between 8-row groups, version 1
 __device__ __forceinline__ unsigned long long tc_desc(unsigned smem_addr) {
   unsigned long long d = 0;
   d |= (unsigned long long)((smem_addr & 0x3FFFF) >> 4);
   d |= (unsigned long long)(128 >> 4) << 16;
-  d |= (unsigned long long)(1024 >> 4) << 32;
+  d |= (unsigned long long)(TC_SBO >> 4) << 32;
   d |= 1ull << 46;
   return d;
 }
@@ -112,142 +118,247 @@ __device__ __forceinline__ void tc_tile(long long t, int n, int& ti, int& tj) {
   ti = tj = 0;
 }
 
-// Prepare pass (all threads of the calling grid, elements split round-robin):
+// four consecutive k of one core-matrix row (16 bytes) in the four
+// sub-images re_hi, re_lo, im_hi, im_lo (sub apart)
+__device__ __forceinline__ void tc_store_split(unsigned char* base, int sub, const float re[4], const float im[4]) {
+  float4 h, l;
+  h.x = tf32_hi(re[0]); h.y = tf32_hi(re[1]); h.z = tf32_hi(re[2]); h.w = tf32_hi(re[3]);
+  l.x = re[0] - h.x; l.y = re[1] - h.y; l.z = re[2] - h.z; l.w = re[3] - h.w;
+  *reinterpret_cast<float4*>(base + 0 * sub) = h;
+  *reinterpret_cast<float4*>(base + 1 * sub) = l;
+  h.x = tf32_hi(im[0]); h.y = tf32_hi(im[1]); h.z = tf32_hi(im[2]); h.w = tf32_hi(im[3]);
+  l.x = im[0] - h.x; l.y = im[1] - h.y; l.z = im[2] - h.z; l.w = im[3] - h.w;
+  *reinterpret_cast<float4*>(base + 2 * sub) = h;
+  *reinterpret_cast<float4*>(base + 3 * sub) = l;
+}
+
+// Prepare pass (all threads of the calling grid, items split round-robin):
 // split images of Y = X diag(alpha) (A side, 128-row blocks) and X (B side,
-// 64-row blocks), for nk = ceil(r / 32) chunks, zero-padded past n and r.
-__device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char* imgA, unsigned char* imgB, long long gtid,
-                           long long gstride) {
-  const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
-  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N - 1) / TC_N;
-  // A side
-  const long long totA = (long long)nI * TC_M * nk * TC_KC;
-  for (long long e = gtid; e < totA; e += gstride) {
-    const int k = (int)(e % TC_KC);
-    long long rest = e / TC_KC;
-    const int row = (int)(rest % TC_M);
-    rest /= TC_M;
-    const int c = (int)(rest % nk);
-    const int I = (int)(rest / nk);
-    const int gi = I * TC_M + row, q = c * TC_KC + k;
-    float yr = 0.f, yi = 0.f;
-    if (gi < n && q < r) {
-      c128 al = a.xa[q];
-      float2 x = a.X[(size_t)gi * a.R + q];
-      float ax = (float)al.x, ay = (float)al.y;
-      yr = fmaf(ax, x.x, -ay * x.y);
-      yi = fmaf(ax, x.y, ay * x.x);
-    }
-    unsigned char* base = imgA + ((size_t)I * nk + c) * TC_ACHUNK + tc_off(row, k);
-    float yr_hi = tf32_hi(yr), yi_hi = tf32_hi(yi);
-    *reinterpret_cast<float*>(base + 0 * TC_ASUB) = yr_hi;
-    *reinterpret_cast<float*>(base + 1 * TC_ASUB) = yr - yr_hi;
-    *reinterpret_cast<float*>(base + 2 * TC_ASUB) = yi_hi;
-    *reinterpret_cast<float*>(base + 3 * TC_ASUB) = yi - yi_hi;
+// 64-row blocks), for nk = ceil(r / TC_KC) chunks, zero-padded past n and r.
+// An item is four consecutive delayed columns of one row: one 32-byte read of
+// X and one 16-byte write per sub-image (four k of a core-matrix row).
+__device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char* imgA, unsigned char* imgB,
+                                        long long gtid, long long gstride) {
+  __shared__ float2 s_al[kMaxDelay];
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    const c128 al = a.xa[q];
+    s_al[q] = make_float2((float)al.x, (float)al.y);
   }
-  // B side
-  const long long totB = (long long)nJ * TC_N * nk * TC_KC;
-  for (long long e = gtid; e < totB; e += gstride) {
-    const int k = (int)(e % TC_KC);
-    long long rest = e / TC_KC;
-    const int row = (int)(rest % TC_N);
-    rest /= TC_N;
-    const int c = (int)(rest % nk);
-    const int J = (int)(rest / nk);
-    const int gj = J * TC_N + row, q = c * TC_KC + k;
-    float xr = 0.f, xi = 0.f;
-    if (gj < n && q < r) {
-      float2 x = a.X[(size_t)gj * a.R + q];
-      xr = x.x;
-      xi = x.y;
+  __syncthreads();
+  const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
+  const unsigned nI = (unsigned)(n + TC_M - 1) / TC_M, nJ = (unsigned)(n + TC_N - 1) / TC_N;
+  constexpr unsigned KQ = TC_KC / 4;  // items per chunk row
+  // A side: item = ((I * nk + c) * TC_M + row) * KQ + kq
+  const unsigned totA = nI * (unsigned)nk * TC_M * KQ;
+  for (unsigned e = (unsigned)gtid; e < totA; e += (unsigned)gstride) {
+    const unsigned kq = e % KQ, row = (e / KQ) % TC_M, rest = e / (KQ * TC_M);
+    const unsigned c = rest % (unsigned)nk, I = rest / (unsigned)nk;
+    const int gi = (int)(I * TC_M + row), q0 = (int)(c * TC_KC + kq * 4);
+    float yr[4], yi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      yr[u] = yi[u] = 0.f;
+      const int q = q0 + u;
+      if (gi < n && q < r) {
+        const float2 x = a.X[(size_t)gi * a.R + q], al = s_al[q];
+        yr[u] = fmaf(al.x, x.x, -al.y * x.y);
+        yi[u] = fmaf(al.x, x.y, al.y * x.x);
+      }
     }
-    unsigned char* base = imgB + ((size_t)J * nk + c) * TC_BCHUNK + tc_off(row, k);
-    float xr_hi = tf32_hi(xr), xi_hi = tf32_hi(xi);
-    *reinterpret_cast<float*>(base + 0 * TC_BSUB) = xr_hi;
-    *reinterpret_cast<float*>(base + 1 * TC_BSUB) = xr - xr_hi;
-    *reinterpret_cast<float*>(base + 2 * TC_BSUB) = xi_hi;
-    *reinterpret_cast<float*>(base + 3 * TC_BSUB) = xi - xi_hi;
+    unsigned char* base = imgA + ((size_t)I * nk + c) * TC_ACHUNK + tc_off((int)row, (int)kq * 4);
+    tc_store_split(base, TC_ASUB, yr, yi);
+  }
+  // B side: item = ((J * nk + c) * TC_N + row) * KQ + kq
+  const unsigned totB = nJ * (unsigned)nk * TC_N * KQ;
+  for (unsigned e = (unsigned)gtid; e < totB; e += (unsigned)gstride) {
+    const unsigned kq = e % KQ, row = (e / KQ) % TC_N, rest = e / (KQ * TC_N);
+    const unsigned c = rest % (unsigned)nk, J = rest / (unsigned)nk;
+    const int gj = (int)(J * TC_N + row), q0 = (int)(c * TC_KC + kq * 4);
+    float xr[4], xi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xr[u] = xi[u] = 0.f;
+      const int q = q0 + u;
+      if (gj < n && q < r) {
+        const float2 x = a.X[(size_t)gj * a.R + q];
+        xr[u] = x.x;
+        xi[u] = x.y;
+      }
+    }
+    unsigned char* base = imgB + ((size_t)J * nk + c) * TC_BCHUNK + tc_off((int)row, (int)kq * 4);
+    tc_store_split(base, TC_BSUB, xr, xi);
   }
   // the images are read next by bulk asynchronous copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Tensor-core state of a CTA.  Barriers 0, 1: operand copies into buffer 0, 1;
+// barriers 2, 3: MMA commits that read buffer 0, 1.  Only thread 0 issues and
+// waits: ph is the parity of the next wait, pend marks an issued operation
+// that has not been waited for.
 struct TcState {
-  unsigned tmem;     // tensor-memory base address of this CTA's accumulators
-  unsigned mb_load;  // mbarrier: bulk copies landed
-  unsigned mb_mma;   // mbarrier: MMAs of a chunk complete
-  unsigned ph_load, ph_mma;
+  unsigned tmem;  // tensor-memory base address of this CTA's accumulators
+  unsigned mb[4];
+  unsigned ph[4];
+  int pend[4];
 };
 
-// Tiles [t_begin, T) with step t_step, by the first 128 threads of the CTA
-// (warp w reads accumulator lanes 32w..32w+31).  Returns false after a timeout.
+// all threads: barriers (thread 0), tensor memory (warp 0), then a CTA barrier
+__device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, unsigned* tmem_slot) {
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) {
+      const unsigned m = (unsigned)__cvta_generic_to_shared(bars + q);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (threadIdx.x < 32) {
+    const unsigned sl = (unsigned)__cvta_generic_to_shared(tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sl), "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  st.tmem = *tmem_slot;
+  for (int q = 0; q < 4; ++q) {
+    st.mb[q] = (unsigned)__cvta_generic_to_shared(bars + q);
+    st.ph[q] = 0;
+    st.pend[q] = 0;
+  }
+}
+
+// thread 0: wait (bounded) for barrier q's pending operation; false on expiry
+__device__ __forceinline__ bool tc_wait(TcState& st, int q) {
+  if (!st.pend[q]) return true;
+  if (!mbar_wait(st.mb[q], st.ph[q])) return false;
+  st.ph[q] ^= 1;
+  st.pend[q] = 0;
+  return true;
+}
+
+// all threads: after a failure thread 0 gives what it issued a bounded time to
+// land (copies first, then the MMA commits), then warp 0 frees the tensor memory
+__device__ __forceinline__ void tc_teardown(TcState& st, bool failed) {
+  if (failed && threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) tc_wait(st, q);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(TC_TMEM_COLS));
+}
+
+// thread 0: bulk copies of K-chunk c of tile (ti, tj) into buffer bf
+__device__ __forceinline__ void tc_issue_copy(TcState& st, int bf, unsigned sbuf, const unsigned char* imgA,
+                                              const unsigned char* imgB, int ti, int tj, int c, int nk) {
+  const unsigned char* ga = imgA + ((size_t)ti * nk + c) * TC_ACHUNK;
+  const unsigned char* gb = imgB + ((size_t)tj * nk + c) * TC_BCHUNK;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(st.mb[bf]), "r"(TC_BUF) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbuf),
+               "l"(ga), "r"(TC_ACHUNK), "r"(st.mb[bf])
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sbuf + TC_ACHUNK),
+               "l"(gb), "r"(TC_BCHUNK), "r"(st.mb[bf])
+               : "memory");
+  st.pend[bf] = 1;
+}
+
+// thread 0: the 3xTF32 products of one K-chunk in buffer sbuf, committed to barrier 2 + bf
+__device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf, bool first_chunk) {
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const unsigned sA = sbuf, sB = sbuf + TC_ACHUNK;
+  const unsigned dR = st.tmem, dI = st.tmem + TC_N;
+  const unsigned id_pos = tc_idesc(false), id_neg = tc_idesc(true);
+#pragma unroll
+  for (int ks = 0; ks < TC_KC / 8; ++ks) {
+    const unsigned ko = 256u * ks;
+    const unsigned long long yr_hi = tc_desc(sA + 0 * TC_ASUB + ko), yr_lo = tc_desc(sA + 1 * TC_ASUB + ko);
+    const unsigned long long yi_hi = tc_desc(sA + 2 * TC_ASUB + ko), yi_lo = tc_desc(sA + 3 * TC_ASUB + ko);
+    const unsigned long long xr_hi = tc_desc(sB + 0 * TC_BSUB + ko), xr_lo = tc_desc(sB + 1 * TC_BSUB + ko);
+    const unsigned long long xi_hi = tc_desc(sB + 2 * TC_BSUB + ko), xi_lo = tc_desc(sB + 3 * TC_BSUB + ko);
+    const unsigned first = (first_chunk && ks == 0) ? 0u : 1u;
+    // Wr += Yr Xr^T - Yi Xi^T
+    tc_mma(dR, yr_hi, xr_hi, id_pos, first);
+    tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
+    tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
+    tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
+    tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
+    tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
+    // Wi += Yr Xi^T + Yi Xr^T
+    tc_mma(dI, yr_hi, xi_hi, id_pos, first);
+    tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
+    tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
+    tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
+    tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
+    tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(st.mb[2 + bf])
+               : "memory");
+  st.pend[2 + bf] = 1;
+}
+
+// Tiles [t_begin, T) with step t_step; thread 0 drives the copies and the
+// MMAs, the first 128 threads read the accumulators (warp w: lanes
+// 32w..32w+31), all threads (at least 256) read and write the tile of W_lo.
+// smem: TC_SMEM bytes.  Returns false after a timeout (the caller then calls
+// tc_teardown with failed = true).
 __device__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* imgA, const unsigned char* imgB,
                               unsigned char* smem, TcState& st, long long t_begin, long long t_step) {
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
   const long long T = tc_tiles(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const unsigned sA = (unsigned)__cvta_generic_to_shared(smem);
-  const unsigned sB = sA + TC_ACHUNK;
+  const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem);
   __shared__ int s_fail;
   if (tid == 0) s_fail = 0;
   __syncthreads();
+  // epilogue items: float4 groups of the 128 x 64 tile, item it = row * 16 + column / 4
+  constexpr int V = 4, PER_ROW = TC_N / V, ITEMS = TC_M * PER_ROW, MAXU = 8;
+  const int nthr = (int)blockDim.x;
+  if (nthr * MAXU < ITEMS) return false;  // every item needs a thread slot (>= 256 threads)
   for (long long t = t_begin; t < T; t += t_step) {
     int ti, tj;
     tc_tile(t, n, ti, tj);
-    for (int c = 0; c < nk; ++c) {
-      if (tid == 0) {
-        const unsigned char* ga = imgA + ((size_t)ti * nk + c) * TC_ACHUNK;
-        const unsigned char* gb = imgB + ((size_t)tj * nk + c) * TC_BCHUNK;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(st.mb_load), "r"(TC_SMEM)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sA),
-                     "l"(ga), "r"(TC_ACHUNK), "r"(st.mb_load)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sB),
-                     "l"(gb), "r"(TC_BCHUNK), "r"(st.mb_load)
-                     : "memory");
-      }
-      if (tid < 128 && !mbar_wait(st.mb_load, st.ph_load)) s_fail = 1;
-      st.ph_load ^= 1;
-      __syncthreads();
-      if (s_fail) return false;
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const unsigned dR = st.tmem, dI = st.tmem + TC_N;
-        const unsigned id_pos = tc_idesc(false), id_neg = tc_idesc(true);
-#pragma unroll
-        for (int ks = 0; ks < TC_KC / 8; ++ks) {
-          const unsigned ko = 256u * ks;
-          const unsigned long long yr_hi = tc_desc(sA + 0 * TC_ASUB + ko), yr_lo = tc_desc(sA + 1 * TC_ASUB + ko);
-          const unsigned long long yi_hi = tc_desc(sA + 2 * TC_ASUB + ko), yi_lo = tc_desc(sA + 3 * TC_ASUB + ko);
-          const unsigned long long xr_hi = tc_desc(sB + 0 * TC_BSUB + ko), xr_lo = tc_desc(sB + 1 * TC_BSUB + ko);
-          const unsigned long long xi_hi = tc_desc(sB + 2 * TC_BSUB + ko), xi_lo = tc_desc(sB + 3 * TC_BSUB + ko);
-          const unsigned first = (c == 0 && ks == 0) ? 0u : 1u;
-          // Wr += Yr Xr^T - Yi Xi^T
-          tc_mma(dR, yr_hi, xr_hi, id_pos, first);
-          tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
-          tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
-          tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
-          tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
-          tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
-          // Wi += Yr Xi^T + Yi Xr^T
-          tc_mma(dI, yr_hi, xi_hi, id_pos, first);
-          tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
-          tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
-          tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
-          tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
-          tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
+    const int i0 = ti * TC_M, j0 = tj * TC_N;
+    if (tid == 0) {
+      // chunk c in buffer c & 1; the copy of chunk c + 1 is issued once the
+      // MMAs of chunk c - 1 (same buffer) have completed
+      bool ok = true;
+      tc_issue_copy(st, 0, s0, imgA, imgB, ti, tj, 0, nk);
+      for (int c = 0; c < nk && ok; ++c) {
+        const int bf = c & 1;
+        if (c + 1 < nk) {
+          ok = tc_wait(st, 2 + (bf ^ 1));
+          if (ok) tc_issue_copy(st, bf ^ 1, s0 + (bf ^ 1) * TC_BUF, imgA, imgB, ti, tj, c + 1, nk);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(st.mb_mma)
-                     : "memory");
+        if (ok) ok = tc_wait(st, bf);
+        if (ok) tc_issue_mma(st, bf, s0 + bf * TC_BUF, c == 0);
       }
-      if (tid < 128 && !mbar_wait(st.mb_mma, st.ph_mma)) s_fail = 1;
-      st.ph_mma ^= 1;
-      __syncthreads();
-      if (s_fail) return false;
+      // the commits complete in order: chunk nk - 2's barrier, then nk - 1's
+      if (ok && nk >= 2) ok = tc_wait(st, 2 + ((nk - 2) & 1));
+      if (ok) ok = tc_wait(st, 2 + ((nk - 1) & 1));
+      if (!ok) s_fail = 1;
     }
-    // epilogue: accumulators -> shared staging -> W_lo (coalesced read-modify-write)
+    // the tile of W_lo is read now, while the copies and the MMAs run
+    float4 wr[MAXU], wi[MAXU];
+    int okv[MAXU];
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+      const int it = tid + u * nthr;
+      const int row = it / PER_ROW, col = (it % PER_ROW) * V;
+      const int gi = i0 + row, gj = j0 + col;
+      okv[u] = (it < ITEMS && gi < n) ? (gj + V <= n ? 2 : (gj < n ? 1 : 0)) : 0;
+      if (okv[u] == 2) {
+        const size_t o = (size_t)gi * a.ldl + gj;
+        wr[u] = *reinterpret_cast<const float4*>(a.Wr + o);
+        wi[u] = *reinterpret_cast<const float4*>(a.Wi + o);
+      }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    // epilogue: accumulators -> shared staging -> W_lo
     asm volatile("tcgen05.fence::after_thread_sync;");
-    float* stage = reinterpret_cast<float*>(smem);  // [2][128][65]
+    float* stage = reinterpret_cast<float*>(smem);  // [2][128][65], over the consumed buffers
     if (tid < 128) {
       const unsigned lane_base = (unsigned)(32 * warp) << 16;
 #pragma unroll
@@ -272,48 +383,25 @@ __device__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* im
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    {
-      // 16-byte accesses, all loads of a thread issued before its stores
-      const int i0 = ti * TC_M, j0 = tj * TC_N;
-      const int nthr = (int)blockDim.x;
-      constexpr int V = 4, PER_ROW = TC_N / V, ITEMS = TC_M * PER_ROW;  // float4 items per plane
-      if (tid < nthr) {
-        for (int base = tid; base < ITEMS; base += nthr * 8) {
-          float4 wr[8], wi[8];
-          int ok[8];
+    // add the accumulators to the prefetched tile and store it
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int it = base + u * nthr;
-            const int row = it / PER_ROW, col = (it % PER_ROW) * V;
-            const int gi = i0 + row, gj = j0 + col;
-            ok[u] = (it < ITEMS && gi < n) ? (gj + V <= n ? 2 : (gj < n ? 1 : 0)) : 0;
-            if (ok[u] == 2) {
-              size_t o = (size_t)gi * a.ldl + gj;
-              wr[u] = *reinterpret_cast<const float4*>(a.Wr + o);
-              wi[u] = *reinterpret_cast<const float4*>(a.Wi + o);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int it = base + u * nthr;
-            if (!ok[u]) continue;
-            const int row = it / PER_ROW, col = (it % PER_ROW) * V;
-            const int gi = i0 + row, gj = j0 + col;
-            const float* sr = stage + (0 * TC_M + row) * (TC_N + 1) + col;
-            const float* si = stage + (1 * TC_M + row) * (TC_N + 1) + col;
-            size_t o = (size_t)gi * a.ldl + gj;
-            if (ok[u] == 2) {
-              wr[u].x += sr[0]; wr[u].y += sr[1]; wr[u].z += sr[2]; wr[u].w += sr[3];
-              wi[u].x += si[0]; wi[u].y += si[1]; wi[u].z += si[2]; wi[u].w += si[3];
-              *reinterpret_cast<float4*>(a.Wr + o) = wr[u];
-              *reinterpret_cast<float4*>(a.Wi + o) = wi[u];
-            } else {
-              for (int q = 0; q < V && gj + q < n; ++q) {
-                a.Wr[o + q] += sr[q];
-                a.Wi[o + q] += si[q];
-              }
-            }
-          }
+    for (int u = 0; u < MAXU; ++u) {
+      const int it = tid + u * nthr;
+      if (!okv[u]) continue;
+      const int row = it / PER_ROW, col = (it % PER_ROW) * V;
+      const int gi = i0 + row, gj = j0 + col;
+      const float* sr = stage + (0 * TC_M + row) * (TC_N + 1) + col;
+      const float* si = stage + (1 * TC_M + row) * (TC_N + 1) + col;
+      const size_t o = (size_t)gi * a.ldl + gj;
+      if (okv[u] == 2) {
+        wr[u].x += sr[0]; wr[u].y += sr[1]; wr[u].z += sr[2]; wr[u].w += sr[3];
+        wi[u].x += si[0]; wi[u].y += si[1]; wi[u].z += si[2]; wi[u].w += si[3];
+        *reinterpret_cast<float4*>(a.Wr + o) = wr[u];
+        *reinterpret_cast<float4*>(a.Wi + o) = wi[u];
+      } else {
+        for (int q = 0; q < V && gj + q < n; ++q) {
+          a.Wr[o + q] += sr[q];
+          a.Wi[o + q] += si[q];
         }
       }
     }
@@ -322,27 +410,6 @@ __device__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* im
     __syncthreads();
   }
   return true;
-}
-
-// tensor memory of the CTA: warp 0 allocates TC_TMEM_COLS columns
-__device__ __forceinline__ void tc_alloc(unsigned* slot) {
-  if (threadIdx.x < 32) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(slot);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s), "r"(TC_TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-}
-__device__ __forceinline__ void tc_free(unsigned tmem) {
-  if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-}
-__device__ __forceinline__ void tc_mbar_init(unsigned long long* mb_load, unsigned long long* mb_mma) {
-  if (threadIdx.x == 0) {
-    unsigned a = (unsigned)__cvta_generic_to_shared(mb_load), b = (unsigned)__cvta_generic_to_shared(mb_mma);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
 }
 
 // bytes of the global operand images for a region of n pixels and r <= R delayed columns

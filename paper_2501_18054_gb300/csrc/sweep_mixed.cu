@@ -214,21 +214,10 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     return true;
   };
   // tensor-core fold: warp 0 holds TC_TMEM_COLS columns of tensor memory for the whole search
-  __shared__ __align__(8) unsigned long long s_mb_load, s_mb_mma;
+  __shared__ __align__(8) unsigned long long s_tc_bars[4];
   __shared__ unsigned s_tmem;
-  TcState tcs;
-  tcs.tmem = 0;
-  tcs.ph_load = tcs.ph_mma = 0;
-  if (a.tensor_fold) {
-    tc_mbar_init(&s_mb_load, &s_mb_mma);
-    tc_alloc(&s_tmem);
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    tcs.tmem = s_tmem;
-    tcs.mb_load = (unsigned)__cvta_generic_to_shared(&s_mb_load);
-    tcs.mb_mma = (unsigned)__cvta_generic_to_shared(&s_mb_mma);
-  }
+  TcState tcs{};
+  if (a.tensor_fold) tc_setup(tcs, s_tc_bars, &s_tmem);
   // the fold reuses the shared memory of the delayed rows: they are in global
   // X as well and the delayed set is empty afterwards
   auto flush = [&]() -> bool {
@@ -237,6 +226,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       tc_prepare(a, r, a.tcimgA, a.tcimgB, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                  (long long)gridDim.x * blockDim.x);
       if (!grid_sync(ctl)) return false;
+      tick(14);
       if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, work, tcs, blockIdx.x, gridDim.x)) {
         if (threadIdx.x == 0) latch_status(ctl, PNGF_ETIMEOUT);
         return false;
@@ -556,16 +546,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   }
   __syncthreads();
   store_et(true);
-  if (a.tensor_fold) {
-    if (failed && threadIdx.x < 128) {
-      // give what this CTA issued a bounded time to land before the free
-      mbar_wait(tcs.mb_load, tcs.ph_load);
-      mbar_wait(tcs.mb_mma, tcs.ph_mma);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    tc_free(tcs.tmem);
-  }
+  if (a.tensor_fold) tc_teardown(tcs, failed);  // after a failure: bounded wait for what was issued
   if (cta == 0 && threadIdx.x == 0) {
     if (failed) status = PNGF_ETIMEOUT;
     FOR_PORTS(p, n_o) ctl->o[p] = cadd(cmul(s_S[p], s_iscale[p]), s_op.off[p]);
