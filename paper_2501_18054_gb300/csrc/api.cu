@@ -62,6 +62,7 @@ Layout make_layout(const pngf_config& cfg) {
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
   L.actg = take(n * sizeof(int));  // active-pixel list of the refresh
+  L.gsum = take(n * n * sizeof(double));  // Re G + Im G (three-multiplication refresh products)
   L.ipiv = take(2 * n * sizeof(int));
   L.snapW = take(L.snapW_bytes);
   L.snapState = take(L.state_bytes + sizeof(Control));

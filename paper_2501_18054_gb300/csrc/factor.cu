@@ -354,6 +354,15 @@ __global__ void __launch_bounds__(256) form_o(const c128* __restrict__ God, cons
   }
 }
 
+// S = Re G + Im G (n x n, row-major), the third real matrix of the refresh's
+// three-multiplication complex products
+__global__ void gsum_kernel(const c128* __restrict__ G, long long nn, double* __restrict__ S) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const c128 g = G[i];
+    S[i] = g.x + g.y;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- driver
@@ -375,6 +384,7 @@ pngf_status factor_fp64(pngf_ctx* c, const uint8_t* b) {
     dim3 grid((n + 255) / 256 > 8 ? 8 : (n + 255) / 256, n);
     build_system<<<grid, 256, 0, s>>>(c->G, c->dv, b, n, ldw, LU, v, bb);
   }
+  gsum_kernel<<<c->n_sm * 4, 256, 0, s>>>(c->G, (long long)n * n, at<double>(c, c->L.gsum));
   // LU with partial pivoting
   for (int j0 = 0; j0 < n; j0 += NB) {
     int jb = n - j0 < NB ? n - j0 : NB;

@@ -33,6 +33,7 @@ struct SweepArgs {
   double* trace_f;
   int64_t* counters;
   const c128* G;
+  const double* Gs;  // Re G + Im G
   const c128* God;
   const c128* cd;
   const c128* co;
@@ -326,13 +327,30 @@ __device__ __forceinline__ c128 warp_sum(c128 v) {
   return v;
 }
 
+// Re x + Im x of the refined vectors, for the three-multiplication products of
+// the residual (block 3 holds them until the correction overwrites it)
+__device__ __forceinline__ double* xsum(const SweepArgs& a, int q) {
+  return reinterpret_cast<double*>(rvec(a, 3, 0)) + (size_t)q * a.n;
+}
+
 // R0: x = v.[e, T] for own pixels
 __device__ void refresh_x(const SweepArgs& a, int pb, int pe) {
   for (int j = pb + threadIdx.x; j < pe; j += blockDim.x) {
     c128 vj = a.v[j];
-    rvec(a, 1, 0)[j] = cmul(vj, a.e[j]);
-    for (int p = 0; p < a.n_o; ++p) rvec(a, 1, 1 + p)[j] = cmul(vj, a.T[(size_t)p * a.ldt + j]);
+    const c128 x0 = cmul(vj, a.e[j]);
+    rvec(a, 1, 0)[j] = x0;
+    xsum(a, 0)[j] = x0.x + x0.y;
+    for (int p = 0; p < a.n_o; ++p) {
+      const c128 xp = cmul(vj, a.T[(size_t)p * a.ldt + j]);
+      rvec(a, 1, 1 + p)[j] = xp;
+      xsum(a, 1 + p)[j] = xp.x + xp.y;
+    }
   }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
 }
 
 // The refresh kernels carry the number of refined vectors NV = 1 + n_o as a
@@ -387,7 +405,10 @@ __device__ __forceinline__ int count_below(const int* act, int m, int v) {
 // R1: residuals of own rows (row j of G dotted with x), and x2 = v.r.  With
 // act (shared memory, room for n entries) only the columns of G at pixels
 // with b_i = 1 are visited: x vanishes elsewhere, so the FP64 work follows the
-// number of "on" pixels instead of n.
+// number of "on" pixels instead of n.  Each complex product runs as Gauss's
+// three real multiplications, (A + iB)(u + iw) = (Au - Bw) + i((A + B)(u + w)
+// - Au - Bw), with A + B precomputed (Gs) and u + w from refresh_x: three FP64
+// FMAs per element and vector instead of four.
 template <int NV>
 __device__ __noinline__ int refresh_residual_t(const SweepArgs& a, int pb, int pe, int* act) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -396,36 +417,48 @@ __device__ __noinline__ int refresh_residual_t(const SweepArgs& a, int pb, int p
     for (int t = threadIdx.x; t < m; t += blockDim.x) a.actg[t] = act[t];
   for (int j = pb + warp; j < pe; j += nw) {
     const c128* g = a.G + (size_t)j * a.n;
-    c128 acc[NV];
+    const double* gs = a.Gs + (size_t)j * a.n;
+    double p1[NV], p2[NV], p3[NV];  // A u, B w, (A + B)(u + w)
 #pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] = mk(0.0, 0.0);
+    for (int q = 0; q < NV; ++q) p1[q] = p2[q] = p3[q] = 0.0;
+    auto madd = [&](int i) {
+      const c128 gi = g[i];
+      const double si = gs[i];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const c128 x = rvec(a, 1, q)[i];
+        p1[q] = fma(gi.x, x.x, p1[q]);
+        p2[q] = fma(gi.y, x.y, p2[q]);
+        p3[q] = fma(si, xsum(a, q)[i], p3[q]);
+      }
+    };
     if (act) {
 #pragma unroll 4
-      for (int t = lane; t < m; t += 32) {
-        const int i = act[t];
-        c128 gi = g[i];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
-      }
+      for (int t = lane; t < m; t += 32) madd(act[t]);
     } else {
 #pragma unroll 4
-      for (int i = lane; i < a.n; i += 32) {
-        c128 gi = g[i];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] = cfma(gi, rvec(a, 1, q)[i], acc[q]);
-      }
+      for (int i = lane; i < a.n; i += 32) madd(i);
     }
+    // lane q takes vector q's sums, then one code path finishes every vector
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      c128 sum = warp_sum(acc[q]);
-      if (lane == 0) {
-        c128 rhs = q == 0 ? a.cd[j] : a.God[(size_t)(q - 1) * a.n + j];
-        c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
-        c128 r = cadd(csub(rhs, y), sum);
-        rvec(a, 0, q)[j] = r;
-        c128 x2 = cmul(a.v[j], r);
-        x2f(a, q)[j] = make_float2((float)x2.x, (float)x2.y);
+      const double s1 = warp_sum_d(p1[q]), s2 = warp_sum_d(p2[q]), s3 = warp_sum_d(p3[q]);
+      if (lane == q) {
+        t1 = s1;
+        t2 = s2;
+        t3 = s3;
       }
+    }
+    if (lane < NV) {
+      const int q = lane;
+      const c128 sum = mk(t1 - t2, t3 - t1 - t2);
+      const c128 rhs = q == 0 ? a.cd[j] : a.God[(size_t)(q - 1) * a.n + j];
+      const c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
+      const c128 r = cadd(csub(rhs, y), sum);
+      rvec(a, 0, q)[j] = r;
+      const c128 x2 = cmul(a.v[j], r);
+      x2f(a, q)[j] = make_float2((float)x2.x, (float)x2.y);
     }
   }
   return m;
@@ -871,6 +904,7 @@ SweepArgs make_args(pngf_ctx* c) {
   a.rbuf = at<c128>(c, L.rbuf);
   a.ctl = at<Control>(c, L.ctl);
   a.G = c->G;
+  a.Gs = at<double>(c, L.gsum);
   a.God = c->God;
   a.cd = c->cd;
   a.co = c->co;
