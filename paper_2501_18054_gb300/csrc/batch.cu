@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   __shared__ int s_k;
   __shared__ long long s_best;
   // tensor-core fold: this CTA holds TC_TMEM_COLS columns of tensor memory for all its runs
-  __shared__ __align__(8) unsigned long long s_tc_bars[4];
+  __shared__ __align__(8) unsigned long long s_tc_bars[TC_NBAR];
   __shared__ unsigned s_tmem;
   const bool use_tc = n_runs > 0 && runs[0].tensor_fold;
   TcState tcs{};
@@ -313,7 +313,7 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
       cudaSuccess)
     return PNGF_ECUDA;
   const bool mixed = c0->cfg.precision == PNGF_MIXED;
-  size_t smem = mixed ? (kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM) : (size_t)max_n * sizeof(c128);
+  size_t smem = mixed ? (kFlushSmem > (size_t)TC_FOLD_SMEM ? kFlushSmem : (size_t)TC_FOLD_SMEM) : (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PNGF_ECUDA;
   int per_sm = 0;

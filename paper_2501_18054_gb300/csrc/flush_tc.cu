@@ -1,6 +1,6 @@
 // Stand-alone launches of the tensor-core fold (see flush_tc.cuh): a prepare
 // pass over the whole grid, then a tile pass of 256-thread CTAs that each own
-// 128 tensor-memory columns.  Used by the single-call accept path when the
+// 256 tensor-memory columns (two accumulators).  Used by the single-call accept path when the
 // delayed set is full; the persistent search runs the same device code.
 #include "flush_tc.cuh"
 
@@ -13,10 +13,10 @@ __global__ void flush_tc_prepare_kernel(SweepArgs a, unsigned char* imgA, unsign
   tc_prepare(a, r, imgA, imgB, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(256, 2) flush_tc_kernel(SweepArgs a, const unsigned char* imgA,
+__global__ void __launch_bounds__(256, 1) flush_tc_kernel(SweepArgs a, const unsigned char* imgA,
                                                        const unsigned char* imgB) {
   extern __shared__ __align__(128) unsigned char tc_dyn[];
-  __shared__ __align__(8) unsigned long long bars[4];
+  __shared__ __align__(8) unsigned long long bars[TC_NBAR];
   __shared__ unsigned tmem_slot;
   const int r = a.ctl->r_delay;
   if (r < a.R) return;
@@ -35,12 +35,12 @@ pngf_status flush_tc_launch(pngf_ctx* c) {
   unsigned char* imgB = imgA + c->L.tcimgA_bytes;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
+    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_FOLD_SMEM) != cudaSuccess)
       return PNGF_ECUDA;
     attr = true;
   }
   flush_tc_prepare_kernel<<<c->n_sm * 4, 256, 0, c->stream>>>(a, imgA, imgB);
-  flush_tc_kernel<<<c->n_sm * 2, 256, TC_SMEM, c->stream>>>(a, imgA, imgB);
+  flush_tc_kernel<<<c->n_sm, 256, TC_FOLD_SMEM, c->stream>>>(a, imgA, imgB);
   return cuda_status(cudaGetLastError());
 }
 

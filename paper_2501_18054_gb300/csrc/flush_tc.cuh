@@ -41,8 +41,13 @@ constexpr int TC_BSUB = TC_N * TC_KC * 4;  // one B sub-image: 8 KB
 constexpr int TC_ACHUNK = 4 * TC_ASUB;     // Yr_hi, Yr_lo, Yi_hi, Yi_lo
 constexpr int TC_BCHUNK = 4 * TC_BSUB;     // Xr_hi, Xr_lo, Xi_hi, Xi_lo
 constexpr int TC_BUF = TC_ACHUNK + TC_BCHUNK;   // one buffer: 48 KB
-constexpr int TC_SMEM = 2 * TC_BUF;             // two buffers: 96 KB
-constexpr int TC_TMEM_COLS = 128;               // Dr: columns 0..63, Di: 64..127
+constexpr int TC_NBUF = 2;                      // operand buffers
+constexpr int TC_PREF = 1;                      // chunks copied ahead of the one multiplied
+constexpr int TC_SMEM = TC_NBUF * TC_BUF;       // 96 KB
+constexpr int TC_SLD = 33;                      // stage row stride (floats): conflict-free column writes
+constexpr int TC_STAGE = 2 * TC_M * TC_SLD * 4;  // half a tile of both planes
+constexpr int TC_FOLD_SMEM = TC_SMEM + TC_STAGE; // shared memory of tc_fold_tiles
+constexpr int TC_TMEM_COLS = 256;               // two accumulators: Dr at 128 a + 0..63, Di at 128 a + 64..127
 constexpr unsigned long long kTcSpin = 1ull << 22;
 
 // byte offset of element (row, k) inside a K-major no-swizzle image of TC_KC
@@ -192,23 +197,34 @@ __device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Tensor-core state of a CTA.  Barriers 0, 1: operand copies into buffer 0, 1;
-// barriers 2, 3: MMA commits that read buffer 0, 1.  Only thread 0 issues and
-// waits: ph is the parity of the next wait, pend marks an issued operation
-// that has not been waited for.
+// Tensor-core state of a CTA, kept across calls of tc_fold_tiles.  Barriers
+// (index): TC_B_LOAD + b operand copies landed in buffer b; TC_B_FREE + b the
+// MMAs reading buffer b completed; TC_B_FULL + a accumulator a complete;
+// TC_B_EMPTY + a accumulator a read back (one arrival per epilogue warp).  ph
+// is the parity of a thread's next wait on a barrier (each role waits on its
+// own barriers, and every phase of those is waited for exactly once, so the
+// parities stay in step across calls); pend marks a phase the producer
+// expects and has not yet waited for.
+constexpr int TC_B_LOAD = 0, TC_B_FREE = TC_NBUF, TC_B_FULL = 2 * TC_NBUF, TC_B_EMPTY = 2 * TC_NBUF + 2;
+constexpr int TC_NBAR = 2 * TC_NBUF + 4;
 struct TcState {
-  unsigned tmem;  // tensor-memory base address of this CTA's accumulators
-  unsigned mb[4];
-  unsigned ph[4];
-  int pend[4];
+  unsigned tmem;  // tensor-memory base address: accumulator a at columns 128 a .. 128 a + 127
+  unsigned mb[TC_NBAR];
+  unsigned ph[TC_NBAR];
+  int pend[TC_NBAR];
 };
+
+// epilogue warps: the last 8 warps of a CTA of at least 16 warps (two per
+// tensor-memory lane quadrant), else the last 4 (one per quadrant)
+__device__ __forceinline__ int tc_epi_warps() { return (blockDim.x >> 5) >= 16 ? 8 : 4; }
 
 // all threads: barriers (thread 0), tensor memory (warp 0), then a CTA barrier
 __device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, unsigned* tmem_slot) {
   if (threadIdx.x == 0) {
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < TC_NBAR; ++q) {
       const unsigned m = (unsigned)__cvta_generic_to_shared(bars + q);
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m));
+      const unsigned count = q >= TC_B_EMPTY ? (unsigned)tc_epi_warps() : 1u;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(m), "r"(count));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -221,54 +237,63 @@ __device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   st.tmem = *tmem_slot;
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < TC_NBAR; ++q) {
     st.mb[q] = (unsigned)__cvta_generic_to_shared(bars + q);
     st.ph[q] = 0;
     st.pend[q] = 0;
   }
 }
 
-// thread 0: wait (bounded) for barrier q's pending operation; false on expiry
-__device__ __forceinline__ bool tc_wait(TcState& st, int q) {
-  if (!st.pend[q]) return true;
+// wait (bounded) for the next phase of barrier q; false on expiry
+__device__ __forceinline__ bool tc_wait_phase(TcState& st, int q) {
   if (!mbar_wait(st.mb[q], st.ph[q])) return false;
   st.ph[q] ^= 1;
+  return true;
+}
+// producer: wait for barrier q's pending operation, if any
+__device__ __forceinline__ bool tc_wait(TcState& st, int q) {
+  if (!st.pend[q]) return true;
+  if (!tc_wait_phase(st, q)) return false;
   st.pend[q] = 0;
   return true;
 }
 
 // all threads: after a failure thread 0 gives what it issued a bounded time to
-// land (copies first, then the MMA commits), then warp 0 frees the tensor memory
+// land (copies, then the MMA commits), then warp 0 frees the tensor memory
 __device__ __forceinline__ void tc_teardown(TcState& st, bool failed) {
   if (failed && threadIdx.x == 0)
-    for (int q = 0; q < 4; ++q) tc_wait(st, q);
+    for (int q = 0; q < TC_B_FULL; ++q) tc_wait(st, q);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (threadIdx.x < 32)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(TC_TMEM_COLS));
 }
 
-// thread 0: bulk copies of K-chunk c of tile (ti, tj) into buffer bf
+// producer: bulk copies of K-chunk c of tile (ti, tj) into buffer bf
 __device__ __forceinline__ void tc_issue_copy(TcState& st, int bf, unsigned sbuf, const unsigned char* imgA,
                                               const unsigned char* imgB, int ti, int tj, int c, int nk) {
   const unsigned char* ga = imgA + ((size_t)ti * nk + c) * TC_ACHUNK;
   const unsigned char* gb = imgB + ((size_t)tj * nk + c) * TC_BCHUNK;
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(st.mb[bf]), "r"(TC_BUF) : "memory");
+  const unsigned mb = st.mb[TC_B_LOAD + bf];
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TC_BUF) : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbuf),
-               "l"(ga), "r"(TC_ACHUNK), "r"(st.mb[bf])
+               "l"(ga), "r"(TC_ACHUNK), "r"(mb)
                : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    sbuf + TC_ACHUNK),
-               "l"(gb), "r"(TC_BCHUNK), "r"(st.mb[bf])
+               "l"(gb), "r"(TC_BCHUNK), "r"(mb)
                : "memory");
-  st.pend[bf] = 1;
+  st.pend[TC_B_LOAD + bf] = 1;
 }
 
-// thread 0: the 3xTF32 products of one K-chunk in buffer sbuf, committed to barrier 2 + bf
-__device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf, bool first_chunk) {
+// producer: the 3xTF32 products of one K-chunk (buffer sbuf) into accumulator
+// dacc (columns dacc .. dacc + 127); commits to TC_B_FREE + bf, and to
+// TC_B_FULL + acc after the tile's last chunk
+__device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf, unsigned dacc, bool first_chunk,
+                                             bool last_chunk, int acc) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const unsigned sA = sbuf, sB = sbuf + TC_ACHUNK;
-  const unsigned dR = st.tmem, dI = st.tmem + TC_N;
+  const unsigned dR = dacc, dI = dacc + TC_N;
   const unsigned id_pos = tc_idesc(false), id_neg = tc_idesc(true);
 #pragma unroll
   for (int ks = 0; ks < TC_KC / 8; ++ks) {
@@ -293,123 +318,184 @@ __device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf,
     tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
     tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
   }
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(st.mb[2 + bf])
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   st.mb[TC_B_FREE + bf])
                : "memory");
-  st.pend[2 + bf] = 1;
+  st.pend[TC_B_FREE + bf] = 1;
+  if (last_chunk) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     st.mb[TC_B_FULL + acc])
+                 : "memory");
+    st.pend[TC_B_EMPTY + acc] = 1;  // the epilogue will arrive once it has read the accumulator
+  }
 }
 
-// Tiles [t_begin, T) with step t_step; thread 0 drives the copies and the
-// MMAs, the first 128 threads read the accumulators (warp w: lanes
-// 32w..32w+31), all threads (at least 256) read and write the tile of W_lo.
-// smem: TC_SMEM bytes.  Returns false after a timeout (the caller then calls
-// tc_teardown with failed = true).
-__device__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* imgA, const unsigned char* imgB,
-                              unsigned char* smem, TcState& st, long long t_begin, long long t_step) {
+// 16 consecutive accumulator columns of this thread's lane (tensor-memory lane
+// quadrant of the warp), as floats
+__device__ __forceinline__ void tc_ld16(unsigned addr, float v[16]) {
+  unsigned u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(u[q]);
+}
+
+// The tiles [t_begin, T) with step t_step, in a pipeline of three roles:
+//   producer (lane 0 of warp 0): operand chunks stream through two shared
+//     buffers across tile boundaries; the MMAs of a tile go to accumulator
+//     k & 1 once the epilogue has read that accumulator's previous tile;
+//   epilogue (the last tc_epi_warps() warps, named barrier 1): per half tile
+//     its threads read their part of W_lo while the tile's MMAs run, copy the
+//     accumulator rows of their lane quadrants (tcgen05.ld) into a shared stage
+//     and add the stage into W_lo with row-contiguous accesses;
+//   the other warps wait at the final barrier.
+// smem: TC_FOLD_SMEM bytes (operand buffers, then the stage).  Returns false
+// after a timeout (the caller then calls tc_teardown with failed = true).
+__device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* imgA,
+                                           const unsigned char* imgB, unsigned char* smem, TcState& st,
+                                           long long t_begin, long long t_step) {
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
   const long long T = tc_tiles(n);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  const int ew = tc_epi_warps(), ew0 = nwarp - ew;
   const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem);
-  __shared__ int s_fail;
-  if (tid == 0) s_fail = 0;
+  __shared__ int s_fail, s_efail;
+  if (tid == 0) s_fail = s_efail = 0;
+  // earlier generic-proxy use of this shared memory before the bulk copies write it
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  // epilogue items: float4 groups of the 128 x 64 tile, item it = row * 16 + column / 4
-  constexpr int V = 4, PER_ROW = TC_N / V, ITEMS = TC_M * PER_ROW, MAXU = 8;
-  const int nthr = (int)blockDim.x;
-  if (nthr * MAXU < ITEMS) return false;  // every item needs a thread slot (>= 256 threads)
-  for (long long t = t_begin; t < T; t += t_step) {
-    int ti, tj;
-    tc_tile(t, n, ti, tj);
-    const int i0 = ti * TC_M, j0 = tj * TC_N;
-    if (tid == 0) {
-      // chunk c in buffer c & 1; the copy of chunk c + 1 is issued once the
-      // MMAs of chunk c - 1 (same buffer) have completed
-      bool ok = true;
-      tc_issue_copy(st, 0, s0, imgA, imgB, ti, tj, 0, nk);
-      for (int c = 0; c < nk && ok; ++c) {
-        const int bf = c & 1;
-        if (c + 1 < nk) {
-          ok = tc_wait(st, 2 + (bf ^ 1));
-          if (ok) tc_issue_copy(st, bf ^ 1, s0 + (bf ^ 1) * TC_BUF, imgA, imgB, ti, tj, c + 1, nk);
+  const long long my_tiles = t_begin < T ? (T - 1 - t_begin) / t_step + 1 : 0;
+  if (tid == 0 && my_tiles > 0) {
+    // ---- producer
+    bool ok = true;
+    const long long total = my_tiles * nk;  // chunks of all this CTA's tiles, in order
+    auto coords = [&](long long g, int& ti, int& tj, int& c) {
+      const long long k = g / nk;
+      c = (int)(g - k * nk);
+      tc_tile(t_begin + k * t_step, n, ti, tj);
+    };
+    for (long long g = 0; g < total && g < TC_PREF; ++g) {  // the first chunks
+      int ti, tj, c;
+      coords(g, ti, tj, c);
+      tc_issue_copy(st, (int)g, s0 + (unsigned)g * TC_BUF, imgA, imgB, ti, tj, c, nk);
+    }
+    for (long long g = 0; g < total && ok; ++g) {
+      const int bf = (int)(g % TC_NBUF);
+      const long long k = g / nk;
+      const int cc = (int)(g - k * nk), acc = (int)(k & 1);
+      const long long gn = g + TC_PREF;
+      if (gn < total) {  // copy chunk gn into its buffer once the MMAs of chunk gn - TC_NBUF are done
+        const int bn = (int)(gn % TC_NBUF);
+        ok = tc_wait(st, TC_B_FREE + bn);
+        int ti2, tj2, c2;
+        coords(gn, ti2, tj2, c2);
+        if (ok) tc_issue_copy(st, bn, s0 + (unsigned)bn * TC_BUF, imgA, imgB, ti2, tj2, c2, nk);
+      }
+      if (ok) ok = tc_wait(st, TC_B_LOAD + bf);
+      // the epilogue has read this accumulator's previous tile (of this call or an earlier one)
+      if (ok && cc == 0) ok = tc_wait(st, TC_B_EMPTY + acc);
+      if (ok) tc_issue_mma(st, bf, s0 + (unsigned)bf * TC_BUF, st.tmem + 128u * acc, cc == 0, cc == nk - 1, acc);
+    }
+    // no copy or MMA still reads the buffers, and every read-back arrival is
+    // consumed, so that the barrier phases of the next call start in step
+    for (int q = TC_B_FREE; q < TC_B_FULL && ok; ++q) ok = tc_wait(st, q);
+    if (ok) ok = tc_wait(st, TC_B_EMPTY) && tc_wait(st, TC_B_EMPTY + 1);
+    if (!ok) s_fail = 1;
+  } else if (warp >= ew0) {
+    // ---- epilogue: per half tile (32 columns of both planes) the warps copy
+    //      their lane quadrant's accumulator rows into the stage, then all
+    //      epilogue threads add the stage into W_lo with row-contiguous accesses
+    const int et = tid - ew0 * 32, ethreads = ew * 32;
+    const int quad = warp & 3, wpq = ew / 4, part = (warp - ew0) >> 2;
+    const int cpw = 32 / wpq;                          // columns of a half per warp
+    const int ipt = TC_M * 8 / ethreads;               // float4 items per thread and plane: 4 or 8
+    float* stage = reinterpret_cast<float*>(smem + TC_SMEM);  // [2 planes][128 rows][TC_SLD]
+    const unsigned lane_base = (unsigned)(32 * quad) << 16;
+    bool ok = true;
+    for (long long k = 0; k < my_tiles && ok; ++k) {
+      int ti, tj;
+      tc_tile(t_begin + k * t_step, n, ti, tj);
+      const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * TC_N;
+      for (int h = 0; h < 2 && ok; ++h) {
+        // this half of W_lo, read before the accumulator is waited for
+        float4 wr[8], wi[8];
+        int okv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          okv[u] = 0;
+          if (u >= ipt) continue;
+          const int it = et + u * ethreads, row = it >> 3, gi = i0 + row, gj = j0 + 32 * h + (it & 7) * 4;
+          okv[u] = gi < n ? (gj + 4 <= n ? 2 : (gj < n ? 1 : 0)) : 0;
+          if (okv[u] == 2) {
+            const size_t o = (size_t)gi * a.ldl + gj;
+            wr[u] = *reinterpret_cast<const float4*>(a.Wr + o);
+            wi[u] = *reinterpret_cast<const float4*>(a.Wi + o);
+          }
         }
-        if (ok) ok = tc_wait(st, bf);
-        if (ok) tc_issue_mma(st, bf, s0 + bf * TC_BUF, c == 0);
-      }
-      // the commits complete in order: chunk nk - 2's barrier, then nk - 1's
-      if (ok && nk >= 2) ok = tc_wait(st, 2 + ((nk - 2) & 1));
-      if (ok) ok = tc_wait(st, 2 + ((nk - 1) & 1));
-      if (!ok) s_fail = 1;
-    }
-    // the tile of W_lo is read now, while the copies and the MMAs run
-    float4 wr[MAXU], wi[MAXU];
-    int okv[MAXU];
-#pragma unroll
-    for (int u = 0; u < MAXU; ++u) {
-      const int it = tid + u * nthr;
-      const int row = it / PER_ROW, col = (it % PER_ROW) * V;
-      const int gi = i0 + row, gj = j0 + col;
-      okv[u] = (it < ITEMS && gi < n) ? (gj + V <= n ? 2 : (gj < n ? 1 : 0)) : 0;
-      if (okv[u] == 2) {
-        const size_t o = (size_t)gi * a.ldl + gj;
-        wr[u] = *reinterpret_cast<const float4*>(a.Wr + o);
-        wi[u] = *reinterpret_cast<const float4*>(a.Wi + o);
-      }
-    }
-    __syncthreads();
-    if (s_fail) return false;
-    // epilogue: accumulators -> shared staging -> W_lo
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    float* stage = reinterpret_cast<float*>(smem);  // [2][128][65], over the consumed buffers
-    if (tid < 128) {
-      const unsigned lane_base = (unsigned)(32 * warp) << 16;
-#pragma unroll
-      for (int half = 0; half < 4; ++half) {  // Dr cols 0-31, 32-63, Di cols 64-95, 96-127
-        unsigned v[32];
-        const unsigned addr = st.tmem + lane_base + 32u * half;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const int plane = half >> 1, col0 = 32 * (half & 1);
-        const int row = 32 * warp + lane;
-#pragma unroll
-        for (int q = 0; q < 32; ++q) stage[(plane * TC_M + row) * (TC_N + 1) + col0 + q] = __uint_as_float(v[q]);
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    // add the accumulators to the prefetched tile and store it
-#pragma unroll
-    for (int u = 0; u < MAXU; ++u) {
-      const int it = tid + u * nthr;
-      if (!okv[u]) continue;
-      const int row = it / PER_ROW, col = (it % PER_ROW) * V;
-      const int gi = i0 + row, gj = j0 + col;
-      const float* sr = stage + (0 * TC_M + row) * (TC_N + 1) + col;
-      const float* si = stage + (1 * TC_M + row) * (TC_N + 1) + col;
-      const size_t o = (size_t)gi * a.ldl + gj;
-      if (okv[u] == 2) {
-        wr[u].x += sr[0]; wr[u].y += sr[1]; wr[u].z += sr[2]; wr[u].w += sr[3];
-        wi[u].x += si[0]; wi[u].y += si[1]; wi[u].z += si[2]; wi[u].w += si[3];
-        *reinterpret_cast<float4*>(a.Wr + o) = wr[u];
-        *reinterpret_cast<float4*>(a.Wi + o) = wi[u];
-      } else {
-        for (int q = 0; q < V && gj + q < n; ++q) {
-          a.Wr[o + q] += sr[q];
-          a.Wi[o + q] += si[q];
+        if (h == 0) {
+          // the decision to stop is taken by all epilogue threads together, so that
+          // none waits at a named barrier that the others have left
+          if (!tc_wait_phase(st, TC_B_FULL + acc)) s_efail = 1;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          asm volatile("bar.sync 1, %0;" ::"r"(ethreads) : "memory");
+          if (s_efail) {
+            ok = false;
+            break;
+          }
         }
+        // accumulator rows of this warp's quadrant -> stage
+        const int row = 32 * quad + lane;
+        for (int c16 = 0; c16 < cpw; c16 += 16) {
+          const int cc = part * cpw + c16;  // column within the half
+          float dr[16], di[16];
+          const unsigned addr = st.tmem + lane_base + 128u * acc + (unsigned)(32 * h + cc);
+          tc_ld16(addr, dr);
+          tc_ld16(addr + TC_N, di);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            stage[(0 * TC_M + row) * TC_SLD + cc + q] = dr[q];
+            stage[(1 * TC_M + row) * TC_SLD + cc + q] = di[q];
+          }
+        }
+        if (h == 1) {  // this warp has read accumulator acc: one arrival per warp
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(st.mb[TC_B_EMPTY + acc]) : "memory");
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ethreads) : "memory");  // stage complete
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (!okv[u]) continue;
+          const int it = et + u * ethreads, rw = it >> 3, c4 = (it & 7) * 4;
+          const int gi = i0 + rw, gj = j0 + 32 * h + c4;
+          const float* sr = stage + (0 * TC_M + rw) * TC_SLD + c4;
+          const float* si = stage + (1 * TC_M + rw) * TC_SLD + c4;
+          const size_t o = (size_t)gi * a.ldl + gj;
+          if (okv[u] == 2) {
+            float4 x = wr[u], y = wi[u];
+            x.x += sr[0]; x.y += sr[1]; x.z += sr[2]; x.w += sr[3];
+            y.x += si[0]; y.y += si[1]; y.z += si[2]; y.w += si[3];
+            *reinterpret_cast<float4*>(a.Wr + o) = x;
+            *reinterpret_cast<float4*>(a.Wi + o) = y;
+          } else {
+            for (int q = 0; q < 4 && gj + q < n; ++q) {
+              a.Wr[o + q] += sr[q];
+              a.Wi[o + q] += si[q];
+            }
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ethreads) : "memory");  // stage consumed
       }
     }
-    // the next tile's bulk copies (async proxy) overwrite the staging area
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (!ok) s_fail = 1;
   }
-  return true;
+  __syncthreads();
+  return s_fail == 0;
 }
 
 // bytes of the global operand images for a region of n pixels and r <= R delayed columns

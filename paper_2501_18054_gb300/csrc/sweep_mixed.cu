@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     return true;
   };
   // tensor-core fold: warp 0 holds TC_TMEM_COLS columns of tensor memory for the whole search
-  __shared__ __align__(8) unsigned long long s_tc_bars[4];
+  __shared__ __align__(8) unsigned long long s_tc_bars[TC_NBAR];
   __shared__ unsigned s_tmem;
   TcState tcs{};
   if (a.tensor_fold) tc_setup(tcs, s_tc_bars, &s_tmem);
@@ -650,7 +650,7 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
-constexpr size_t kMixedWork = kFlushSmem > (size_t)TC_SMEM ? kFlushSmem : (size_t)TC_SMEM;
+constexpr size_t kMixedWork = kFlushSmem > (size_t)TC_FOLD_SMEM ? kFlushSmem : (size_t)TC_FOLD_SMEM;
 static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
 static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
 static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
