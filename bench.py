@@ -33,6 +33,29 @@ METRIC = "DBS pixel-flip evals/sec at N_d=4096, mixed vs FP64 at 1e-4 S-param er
 UNIT = "evals/s"
 WORKLOAD = "fdfd256_nd4096"  # 256^2 FDFD, 16-cell PML, eps=2.2 slab, 64x64 design {1,10}, 2 ports
 
+# DRAM traffic of the search kernel from one ncu capture (profiles/dbs_mixed_kernel_fdfd256_nd4096.md:
+# one launch = one full run, seed 0): measured read + write bytes over the algorithmic bytes of
+# that launch.  A step's traffic is this ratio times the step's algorithmic bytes, reported only
+# while the kernel sources are the captured ones (fingerprint below), else null.
+TRAFFIC_CAPTURE = {"kernel": "dbs_mixed_kernel", "workload": "fdfd256_nd4096",
+                   "measured_bytes": 6.210275e9 + 1.134502e9, "algorithmic_bytes": 5666963456.0,
+                   "sources_sha256": "5b3991cf25a0cc35356af017cd17115bb2e8fb3d310b381d9d41a6ff91cd0be6"}
+
+
+def sources_fingerprint() -> str:
+    """sha256 over the kernel sources (csrc/*.cu, *.cuh) and the C ABI header."""
+    import glob
+    import hashlib
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2501_18054_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_2501_18054_gb300", "csrc", "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "pngf.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -504,8 +527,15 @@ def main():
         bytes_alg = (n_flush * 16.0 * tri + n_ref * (16.0 * n * n + 8.0 * tri) + acc_per_step * 8.0 * n
                      + evals_per_step * (3 + n_o) * 16.0)
         gbs = bytes_alg / (step_ms / 1e3) / 1e9
+        traffic, traffic_note = None, "no capture of the current kernel sources"
+        if args.workload == TRAFFIC_CAPTURE["workload"] and sources_fingerprint() == TRAFFIC_CAPTURE["sources_sha256"]:
+            ratio = TRAFFIC_CAPTURE["measured_bytes"] / TRAFFIC_CAPTURE["algorithmic_bytes"]
+            traffic = ratio * bytes_alg
+            traffic_note = ("bytes per step: ncu dram read + write of one captured launch (one run, seed 0) "
+                            "= %.3f x its algorithmic bytes, scaled to this step's algorithmic bytes" % ratio)
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "traffic": None, "kernel": "dbs_mixed_kernel",
+                    "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_step": bytes_alg,
+                    "kernel": "dbs_mixed_kernel",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
                     "note": "each run keeps one flip at a time (a latency-bound chain of word exchange, "
                             "fetch and FP64 state update per kept flip) and refreshes e, T in FP64 (FP64-pipe "
