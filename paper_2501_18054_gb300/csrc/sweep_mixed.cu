@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   unsigned char* work = reinterpret_cast<unsigned char*>(dyn_smem) + kOwnStateSmem;
   __shared__ int s_pos[kOwnMax];
   __shared__ unsigned char s_b[kOwnMax];
-  __shared__ float2 s_wk[kOwnMax], s_sum[kOwnMax];
+  __shared__ float2 s_wk[kOwnMax];
+  __shared__ float2 s_part[16 * kOwnMax];        // partial delayed sums (U2)
+  __shared__ c128 s_c[kOwnMax], s_ac[kOwnMax];  // column entry c_j and alpha c_j of the kept flip
   __shared__ float2 s_beta[kMaxDelay], s_alpha[kMaxDelay];
   __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
   __shared__ c128 s_o[kMaxPorts];      // port amplitudes after a refresh
@@ -131,7 +133,9 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ Pivot s_pv;
   __shared__ ObjParams s_op;
   __shared__ int s_fail, s_bad;
-  float2* Xs = reinterpret_cast<float2*>(work);  // [own][R] delayed rows, between folds
+  // delayed columns of the own pixels between folds, column-major: Xs[i * OS + jl] = x_i[pb + jl]
+  float2* Xs = reinterpret_cast<float2*>(work);
+  const int OS = (own + 31) & ~31;
   const int R = a.R;
   int r = ctl->r_delay;
   if (tid == 0) {
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   }
   for (int q = tid; q < own * r; q += blockDim.x) {
     const int jl = q / r, i = q - jl * r;
-    Xs[jl * R + i] = a.X[(size_t)(pb + jl) * R + i];
+    Xs[i * OS + jl] = a.X[(size_t)(pb + jl) * R + i];
   }
   for (int i = tid; i < r; i += blockDim.x) {
     c128 al = a.xa[i];
@@ -445,52 +449,73 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     }
     ++acc_in_sweep;
     ++n_acc;
-    // U2: a 16-lane group per own pixel forms the delayed sum in FP32 and the
-    // column entry c_j = W_lo(k, j) + sum_i beta_i x_i[j] (FP32)
+    // U2: the delayed sums sum_i beta_i x_i[j] in FP32.  Own pixels in blocks of
+    // 32 (lane = pixel, consecutive words); the delayed columns split over
+    // `parts` warps per block, whose partial sums meet in shared memory.
     {
-      const int g = tid >> 4, gl = tid & 15;
-      const unsigned half = 0xffffu << (tid & 16);
-      for (int jl = g; jl < own; jl += kThreads / 16) {
-        const float2* xj = Xs + jl * R;
-        float px = 0.f, py = 0.f;
-        for (int i = gl; i < r; i += 16) {
-          float2 b = s_beta[i], x = xj[i];
-          px = fmaf(b.x, x.x, fmaf(-b.y, x.y, px));
-          py = fmaf(b.x, x.y, fmaf(b.y, x.x, py));
+      const int nb = (own + 31) >> 5;
+      const int parts = nb <= 2 ? 8 : 4;
+      if (warp < nb * parts) {
+        const int jl = (warp % nb) * 32 + lane, part = warp / nb;
+        float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+        if (jl < own) {
+          int i = part;
+          for (; i + parts < r; i += 2 * parts) {
+            const float2 b0 = s_beta[i], x0 = Xs[i * OS + jl];
+            const float2 b1 = s_beta[i + parts], x1 = Xs[(i + parts) * OS + jl];
+            ax = fmaf(b0.x, x0.x, fmaf(-b0.y, x0.y, ax));
+            ay = fmaf(b0.x, x0.y, fmaf(b0.y, x0.x, ay));
+            bx = fmaf(b1.x, x1.x, fmaf(-b1.y, x1.y, bx));
+            by = fmaf(b1.x, x1.y, fmaf(b1.y, x1.x, by));
+          }
+          if (i < r) {
+            const float2 b0 = s_beta[i], x0 = Xs[i * OS + jl];
+            ax = fmaf(b0.x, x0.x, fmaf(-b0.y, x0.y, ax));
+            ay = fmaf(b0.x, x0.y, fmaf(b0.y, x0.x, ay));
+          }
+          s_part[part * kOwnMax + jl] = make_float2(ax + bx, ay + by);
         }
-        for (int off = 8; off > 0; off >>= 1) {
-          px += __shfl_xor_sync(half, px, off);
-          py += __shfl_xor_sync(half, py, off);
+      }
+      __syncthreads();
+      // c_j = W_lo(k, j) + delayed sum in FP32, promoted; alpha c_j in FP64; the
+      // column is appended to the delayed set (one thread per own pixel)
+      if (tid < own) {
+        const int jl = tid;
+        float sx = s_wk[jl].x, sy = s_wk[jl].y, dx = 0.f, dy = 0.f;
+        for (int q = 0; q < parts; ++q) {
+          dx += s_part[q * kOwnMax + jl].x;
+          dy += s_part[q * kOwnMax + jl].y;
         }
-        if (gl == 0) s_sum[jl] = make_float2(s_wk[jl].x + px, s_wk[jl].y + py);
+        const float2 cf = make_float2(sx + dx, sy + dy);
+        const c128 cj = mk((double)cf.x, (double)cf.y);
+        s_c[jl] = cj;
+        s_ac[jl] = cmul(s_pv.alpha, cj);
+        const int j = pb + jl;
+        Xs[r * OS + jl] = cf;
+        a.X[(size_t)j * R + r] = cf;
+        if (j == k) {
+          const unsigned char nb2 = s_b[jl] ^ 1;
+          s_b[jl] = nb2;
+          a.b[j] = nb2;
+          a.v[j] = nb2 ? s_dv[jl] : mk(0.0, 0.0);
+        }
       }
     }
     __syncthreads();
     tick(13);
-    // U3: FP64 state update; quantity q (0: diag and the appended column,
-    // 1: e, 2 + p: row p of T') on warps of different sub-partitions
+    // U3: one complex FMA per pixel and quantity q (0: diag, 1: e, 2 + p: row p
+    // of T'), the quantities on warps of different sub-partitions
     {
       const int nq = 2 + n_o;
       for (int q = warp & 3; q < nq; q += 4)
         for (int jl = (warp >> 2) * 32 + lane; jl < own; jl += kThreads / 4) {
-          const float2 cf = s_sum[jl];
-          const c128 cj = mk((double)cf.x, (double)cf.y);
           if (q == 0) {
-            const int j = pb + jl;
-            Xs[jl * R + r] = cf;
-            a.X[(size_t)j * R + r] = cf;
-            s_diag[jl] = cfma(cmul(s_pv.alpha, cj), cj, s_diag[jl]);
-            if (j == k) {
-              const unsigned char nb = s_b[jl] ^ 1;
-              s_b[jl] = nb;
-              a.b[j] = nb;
-              a.v[j] = nb ? s_dv[jl] : mk(0.0, 0.0);
-            }
+            s_diag[jl] = cfma(s_ac[jl], s_c[jl], s_diag[jl]);
           } else if (q == 1) {
-            s_e[jl] = cfma(s_pv.coef, cj, s_e[jl]);
+            s_e[jl] = cfma(s_pv.coef, s_c[jl], s_e[jl]);
           } else {
             c128* tq = s_T + (q - 2) * kOwnMax + jl;
-            *tq = cfma(cmul(s_pv.alpha, cj), s_pv.Tk[q - 2], *tq);
+            *tq = cfma(s_ac[jl], s_pv.Tk[q - 2], *tq);
           }
         }
     }
