@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
   __shared__ c128 s_o[kMaxPorts];      // port amplitudes after a refresh
   __shared__ c128 s_iscale[kMaxPorts];  // 1 / scale_p
-  __shared__ double s_f;
+  __shared__ double s_f, s_thr, s_fthr;  // objective, acceptance margin, improvement bound
   __shared__ Pivot s_pv;
   __shared__ ObjParams s_op;
   __shared__ int s_fail, s_bad;
@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       s_S[p] = cmul(csub(ctl->o[p], a.op.off[p]), a.op.scale[p]);
     }
     s_f = ctl->f;
+    s_thr = accept_threshold(a.op, s_f);
+    s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? s_f + s_thr : s_f - s_thr;
     s_fail = 0;
   }
   for (int jl = tid; jl < own; jl += blockDim.x) {
@@ -249,10 +251,10 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   }
   const long long max_steps = a.n_sweeps;
   while (!failed && status != PNGF_EINVAL) {
-    const double f = s_f;
-    const double thr = accept_threshold(s_op, f);
-    // improving: f_new > f + thr (maximised) or f_new < f - thr (minimised)
-    const double fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? f + thr : f - thr;
+    // improving: f_new > f + thr (maximised) or f_new < f - thr (minimised); the
+    // bounds are formed once per kept flip by the thread that sets f, so that
+    // the warps that do not score issue no FP64 instruction here
+    const double f = s_f, thr = s_thr, fthr = s_fthr;
     const int par = (int)(round & 1);
     const unsigned seq = (unsigned)((round + 1) & kSeqMask);
     unsigned long long* words = a.slots + (size_t)par * P * kSlotStride;
@@ -406,6 +408,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           s_pv.alpha = al;
           s_pv.coef = co;
           s_f = fnew;
+          s_thr = accept_threshold(s_op, fnew);
+          s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fnew + s_thr : fnew - s_thr;
           s_bad = !isfinite(fnew);
         }
       } else if (warp == 5) {
@@ -550,7 +554,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         load_et();
         ports_total(a, s_o);
         if (tid < n_o) s_S[tid] = cmul(csub(s_o[tid], s_op.off[tid]), s_op.scale[tid]);
-        if (tid == 32) s_f = objective_of(s_op, s_o);
+        if (tid == 32) {
+          s_f = objective_of(s_op, s_o);
+          s_thr = accept_threshold(s_op, s_f);
+          s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? s_f + s_thr : s_f - s_thr;
+        }
         __syncthreads();
         tick(5);
       }
