@@ -70,12 +70,12 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   __shared__ float2 s_beta[kMaxDelay];
   __shared__ int s_k;
   __shared__ long long s_best;
-  // tensor-core fold: this CTA holds TC_TMEM_COLS columns of tensor memory for all its runs
+  // tensor-core fold (tiles of 128 x 64): this CTA holds tc_tmem_cols(1) columns of tensor memory for all its runs
   __shared__ __align__(8) unsigned long long s_tc_bars[TC_NBAR];
   __shared__ unsigned s_tmem;
   const bool use_tc = n_runs > 0 && runs[0].tensor_fold;
   TcState tcs{};
-  if (use_tc) tc_setup(tcs, s_tc_bars, &s_tmem);
+  if (use_tc) tc_setup(tcs, s_tc_bars, &s_tmem, tc_tmem_cols(1));
   bool tc_failed = false;
   for (int run = blockIdx.x; run < n_runs && !tc_failed; run += gridDim.x) {
     const SweepArgs& a = runs[run];
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
             tc_prepare(a, r, a.tcimgA, a.tcimgB, threadIdx.x, blockDim.x);
             __threadfence_block();
             __syncthreads();
-            if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, dyn, tcs, 0, 1)) {
+            if (!tc_fold_tiles<1>(a, r, a.tcimgA, a.tcimgB, dyn, tcs, 0, 1)) {
               status = PNGF_ETIMEOUT;
               tc_failed = true;
               break;
@@ -313,7 +313,7 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
       cudaSuccess)
     return PNGF_ECUDA;
   const bool mixed = c0->cfg.precision == PNGF_MIXED;
-  size_t smem = mixed ? (kFlushSmem > (size_t)TC_FOLD_SMEM ? kFlushSmem : (size_t)TC_FOLD_SMEM) : (size_t)max_n * sizeof(c128);
+  size_t smem = mixed ? (kFlushSmem > (size_t)tc_fold_smem(1) ? kFlushSmem : (size_t)tc_fold_smem(1)) : (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PNGF_ECUDA;
   int per_sm = 0;

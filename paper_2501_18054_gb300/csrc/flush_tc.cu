@@ -21,8 +21,8 @@ __global__ void __launch_bounds__(256, 1) flush_tc_kernel(SweepArgs a, const uns
   const int r = a.ctl->r_delay;
   if (r < a.R) return;
   TcState st{};
-  tc_setup(st, bars, &tmem_slot);
-  const bool ok = tc_fold_tiles(a, r, imgA, imgB, tc_dyn, st, blockIdx.x, gridDim.x);
+  tc_setup(st, bars, &tmem_slot, tc_tmem_cols(2));
+  const bool ok = tc_fold_tiles<2>(a, r, imgA, imgB, tc_dyn, st, blockIdx.x, gridDim.x);
   if (!ok && threadIdx.x == 0) latch_status(a.ctl, PNGF_ETIMEOUT);
   tc_teardown(st, !ok);  // after a failure: bounded wait for what was issued
 }
@@ -35,12 +35,12 @@ pngf_status flush_tc_launch(pngf_ctx* c) {
   unsigned char* imgB = imgA + c->L.tcimgA_bytes;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_FOLD_SMEM) != cudaSuccess)
+    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fold_smem(2)) != cudaSuccess)
       return PNGF_ECUDA;
     attr = true;
   }
   flush_tc_prepare_kernel<<<c->n_sm * 4, 256, 0, c->stream>>>(a, imgA, imgB);
-  flush_tc_kernel<<<c->n_sm, 256, TC_FOLD_SMEM, c->stream>>>(a, imgA, imgB);
+  flush_tc_kernel<<<c->n_sm, 256, tc_fold_smem(2), c->stream>>>(a, imgA, imgB);
   return cuda_status(cudaGetLastError());
 }
 

@@ -9,7 +9,8 @@
 // and lo = a - hi, and hi.hi + hi.lo + lo.hi is accumulated in FP32 in tensor
 // memory, which keeps the fold at FP32 accuracy (the rounding of W_lo itself).
 //
-// Data flow per tile (128 rows x 64 columns, both planes):
+// Data flow per tile (128 rows x 64 NB columns, both planes; NB = 2 for the
+// persistent search, whose A chunk then serves twice as many outputs):
 //   1. a prepare pass writes the split operands once per fold into global
 //      images laid out exactly as the shared-memory tiles (K-major, no
 //      swizzle: 8-row x 16-byte core matrices, 128 B apart along K, 1024 B
@@ -40,14 +41,19 @@ constexpr int TC_ASUB = TC_M * TC_KC * 4;  // one A sub-image (hi or lo, re or i
 constexpr int TC_BSUB = TC_N * TC_KC * 4;  // one B sub-image: 8 KB
 constexpr int TC_ACHUNK = 4 * TC_ASUB;     // Yr_hi, Yr_lo, Yi_hi, Yi_lo
 constexpr int TC_BCHUNK = 4 * TC_BSUB;     // Xr_hi, Xr_lo, Xi_hi, Xi_lo
-constexpr int TC_BUF = TC_ACHUNK + TC_BCHUNK;   // one buffer: 48 KB
 constexpr int TC_NBUF = 2;                      // operand buffers
 constexpr int TC_PREF = 1;                      // chunks copied ahead of the one multiplied
-constexpr int TC_SMEM = TC_NBUF * TC_BUF;       // 96 KB
-constexpr int TC_SLD = 33;                      // stage row stride (floats): conflict-free column writes
-constexpr int TC_STAGE = 2 * TC_M * TC_SLD * 4;  // half a tile of both planes
-constexpr int TC_FOLD_SMEM = TC_SMEM + TC_STAGE; // shared memory of tc_fold_tiles
-constexpr int TC_TMEM_COLS = 256;               // two accumulators: Dr at 128 a + 0..63, Di at 128 a + 64..127
+constexpr int TC_PC = 16;                       // tile columns per epilogue part
+constexpr int TC_STAGE = 2 * TC_M * TC_PC * 4;  // one part of both planes: 16 KB
+// A tile of the fold is 128 rows x 64 NB columns: NB 64-row blocks of X
+// (B operand) share one 128-row block of Y (A operand), NB = 1 or 2.
+__host__ __device__ constexpr int tc_buf_bytes(int nb) { return TC_ACHUNK + nb * TC_BCHUNK; }  // 48 / 64 KB
+// float4 slot of stage row `row`, column group q4 (4 columns): the XOR spreads
+// both the row-per-lane writes and the row-contiguous reads over all banks
+__device__ __forceinline__ int tc_stage_slot(int row, int q4) { return row * 4 + (q4 ^ ((row >> 1) & 3)); }
+__host__ __device__ constexpr int tc_fold_smem(int nb) { return TC_NBUF * tc_buf_bytes(nb) + TC_STAGE; }
+// tensor memory: two accumulators of NB x (Dr: 64 columns, Di: 64 columns)
+__host__ __device__ constexpr int tc_tmem_cols(int nb) { return 2 * 128 * nb; }
 constexpr unsigned long long kTcSpin = 1ull << 22;
 
 // byte offset of element (row, k) inside a K-major no-swizzle image of TC_KC
@@ -103,19 +109,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned phase) {
   return false;
 }
 
-// number of tiles (128-row block ti, 64-column block tj >= 2 ti) and the tile of index t
+// 64-row blocks of the B image, padded to an even count (the pad holds zeros)
+__host__ __device__ __forceinline__ int tc_nj64(int n) { return ((n + TC_N - 1) / TC_N + 1) & ~1; }
+
+// number of tiles (128-row block ti, 64 NB-column block tj >= 2 ti / NB) and the tile of index t
+template <int NB>
 __device__ __forceinline__ long long tc_tiles(int n) {
-  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N - 1) / TC_N;
+  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N * NB - 1) / (TC_N * NB);
   long long T = 0;
-  for (int ti = 0; ti < nI; ++ti) T += max(0, nJ - 2 * ti);
+  for (int ti = 0; ti < nI; ++ti) T += max(0, nJ - 2 * ti / NB);
   return T;
 }
+template <int NB>
 __device__ __forceinline__ void tc_tile(long long t, int n, int& ti, int& tj) {
-  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N - 1) / TC_N;
+  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N * NB - 1) / (TC_N * NB);
   for (ti = 0; ti < nI; ++ti) {
-    long long cnt = max(0, nJ - 2 * ti);
+    long long cnt = max(0, nJ - 2 * ti / NB);
     if (t < cnt) {
-      tj = 2 * ti + (int)t;
+      tj = 2 * ti / NB + (int)t;
       return;
     }
     t -= cnt;
@@ -151,7 +162,7 @@ __device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char
   }
   __syncthreads();
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
-  const unsigned nI = (unsigned)(n + TC_M - 1) / TC_M, nJ = (unsigned)(n + TC_N - 1) / TC_N;
+  const unsigned nI = (unsigned)(n + TC_M - 1) / TC_M, nJ = (unsigned)tc_nj64(n);
   constexpr unsigned KQ = TC_KC / 4;  // items per chunk row
   // A side: item = ((I * nk + c) * TC_M + row) * KQ + kq
   const unsigned totA = nI * (unsigned)nk * TC_M * KQ;
@@ -208,7 +219,8 @@ __device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char
 constexpr int TC_B_LOAD = 0, TC_B_FREE = TC_NBUF, TC_B_FULL = 2 * TC_NBUF, TC_B_EMPTY = 2 * TC_NBUF + 2;
 constexpr int TC_NBAR = 2 * TC_NBUF + 4;
 struct TcState {
-  unsigned tmem;  // tensor-memory base address: accumulator a at columns 128 a .. 128 a + 127
+  unsigned tmem;       // tensor-memory base address: accumulator a at columns a tmem_cols / 2 ..
+  unsigned tmem_cols;  // columns allocated: tc_tmem_cols(NB) of the fold that uses them
   unsigned mb[TC_NBAR];
   unsigned ph[TC_NBAR];
   int pend[TC_NBAR];
@@ -219,7 +231,7 @@ struct TcState {
 __device__ __forceinline__ int tc_epi_warps() { return (blockDim.x >> 5) >= 16 ? 8 : 4; }
 
 // all threads: barriers (thread 0), tensor memory (warp 0), then a CTA barrier
-__device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, unsigned* tmem_slot) {
+__device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, unsigned* tmem_slot, int tmem_cols) {
   if (threadIdx.x == 0) {
     for (int q = 0; q < TC_NBAR; ++q) {
       const unsigned m = (unsigned)__cvta_generic_to_shared(bars + q);
@@ -230,13 +242,14 @@ __device__ __forceinline__ void tc_setup(TcState& st, unsigned long long* bars, 
   }
   if (threadIdx.x < 32) {
     const unsigned sl = (unsigned)__cvta_generic_to_shared(tmem_slot);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sl), "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sl), "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   st.tmem = *tmem_slot;
+  st.tmem_cols = (unsigned)tmem_cols;
   for (int q = 0; q < TC_NBAR; ++q) {
     st.mb[q] = (unsigned)__cvta_generic_to_shared(bars + q);
     st.ph[q] = 0;
@@ -266,57 +279,67 @@ __device__ __forceinline__ void tc_teardown(TcState& st, bool failed) {
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(st.tmem_cols));
 }
 
-// producer: bulk copies of K-chunk c of tile (ti, tj) into buffer bf
+// producer: bulk copies of K-chunk c of tile (ti, tj) into buffer bf: the A
+// chunk of row block ti, then the B chunks of the NB column blocks NB tj + s
+template <int NB>
 __device__ __forceinline__ void tc_issue_copy(TcState& st, int bf, unsigned sbuf, const unsigned char* imgA,
                                               const unsigned char* imgB, int ti, int tj, int c, int nk) {
-  const unsigned char* ga = imgA + ((size_t)ti * nk + c) * TC_ACHUNK;
-  const unsigned char* gb = imgB + ((size_t)tj * nk + c) * TC_BCHUNK;
   const unsigned mb = st.mb[TC_B_LOAD + bf];
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TC_BUF) : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tc_buf_bytes(NB)) : "memory");
+  const unsigned char* ga = imgA + ((size_t)ti * nk + c) * TC_ACHUNK;
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbuf),
                "l"(ga), "r"(TC_ACHUNK), "r"(mb)
                : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   sbuf + TC_ACHUNK),
-               "l"(gb), "r"(TC_BCHUNK), "r"(mb)
-               : "memory");
+#pragma unroll
+  for (int sb = 0; sb < NB; ++sb) {
+    const unsigned char* gb = imgB + ((size_t)(NB * tj + sb) * nk + c) * TC_BCHUNK;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sbuf + TC_ACHUNK + sb * TC_BCHUNK),
+                 "l"(gb), "r"(TC_BCHUNK), "r"(mb)
+                 : "memory");
+  }
   st.pend[TC_B_LOAD + bf] = 1;
 }
 
 // producer: the 3xTF32 products of one K-chunk (buffer sbuf) into accumulator
-// dacc (columns dacc .. dacc + 127); commits to TC_B_FREE + bf, and to
-// TC_B_FULL + acc after the tile's last chunk
+// dacc (B block s: Dr at dacc + 128 s, Di at dacc + 128 s + 64); commits to
+// TC_B_FREE + bf, and to TC_B_FULL + acc after the tile's last chunk
+template <int NB>
 __device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf, unsigned dacc, bool first_chunk,
                                              bool last_chunk, int acc) {
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const unsigned sA = sbuf, sB = sbuf + TC_ACHUNK;
-  const unsigned dR = dacc, dI = dacc + TC_N;
+  const unsigned sA = sbuf;
   const unsigned id_pos = tc_idesc(false), id_neg = tc_idesc(true);
 #pragma unroll
   for (int ks = 0; ks < TC_KC / 8; ++ks) {
     const unsigned ko = 256u * ks;
     const unsigned long long yr_hi = tc_desc(sA + 0 * TC_ASUB + ko), yr_lo = tc_desc(sA + 1 * TC_ASUB + ko);
     const unsigned long long yi_hi = tc_desc(sA + 2 * TC_ASUB + ko), yi_lo = tc_desc(sA + 3 * TC_ASUB + ko);
-    const unsigned long long xr_hi = tc_desc(sB + 0 * TC_BSUB + ko), xr_lo = tc_desc(sB + 1 * TC_BSUB + ko);
-    const unsigned long long xi_hi = tc_desc(sB + 2 * TC_BSUB + ko), xi_lo = tc_desc(sB + 3 * TC_BSUB + ko);
     const unsigned first = (first_chunk && ks == 0) ? 0u : 1u;
-    // Wr += Yr Xr^T - Yi Xi^T
-    tc_mma(dR, yr_hi, xr_hi, id_pos, first);
-    tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
-    tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
-    tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
-    tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
-    tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
-    // Wi += Yr Xi^T + Yi Xr^T
-    tc_mma(dI, yr_hi, xi_hi, id_pos, first);
-    tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
-    tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
-    tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
-    tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
-    tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
+#pragma unroll
+    for (int sb = 0; sb < NB; ++sb) {
+      const unsigned sB = sbuf + TC_ACHUNK + sb * TC_BCHUNK;
+      const unsigned long long xr_hi = tc_desc(sB + 0 * TC_BSUB + ko), xr_lo = tc_desc(sB + 1 * TC_BSUB + ko);
+      const unsigned long long xi_hi = tc_desc(sB + 2 * TC_BSUB + ko), xi_lo = tc_desc(sB + 3 * TC_BSUB + ko);
+      const unsigned dR = dacc + 128u * sb, dI = dR + TC_N;
+      // Wr += Yr Xr^T - Yi Xi^T
+      tc_mma(dR, yr_hi, xr_hi, id_pos, first);
+      tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
+      tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
+      tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
+      tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
+      tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
+      // Wi += Yr Xi^T + Yi Xr^T
+      tc_mma(dI, yr_hi, xi_hi, id_pos, first);
+      tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
+      tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
+      tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
+      tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
+      tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
+    }
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    st.mb[TC_B_FREE + bf])
@@ -348,19 +371,22 @@ __device__ __forceinline__ void tc_ld16(unsigned addr, float v[16]) {
 //   producer (lane 0 of warp 0): operand chunks stream through two shared
 //     buffers across tile boundaries; the MMAs of a tile go to accumulator
 //     k & 1 once the epilogue has read that accumulator's previous tile;
-//   epilogue (the last tc_epi_warps() warps, named barrier 1): per half tile
-//     its threads read their part of W_lo while the tile's MMAs run, copy the
+//   epilogue (the last tc_epi_warps() warps, named barrier 1): per 16-column
+//     part its threads read their part of W_lo while the tile's MMAs run, copy the
 //     accumulator rows of their lane quadrants (tcgen05.ld) into a shared stage
 //     and add the stage into W_lo with row-contiguous accesses;
 //   the other warps wait at the final barrier.
-// smem: TC_FOLD_SMEM bytes (operand buffers, then the stage).  Returns false
+// smem: tc_fold_smem(NB) bytes (operand buffers, then the stage).  Returns false
 // after a timeout (the caller then calls tc_teardown with failed = true).
+template <int NB>
 __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsigned char* imgA,
                                            const unsigned char* imgB, unsigned char* smem, TcState& st,
                                            long long t_begin, long long t_step) {
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
-  const long long T = tc_tiles(n);
+  const long long T = tc_tiles<NB>(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  constexpr int BUF = tc_buf_bytes(NB);
+  constexpr unsigned ACC = 128u * NB;  // tensor-memory columns of one accumulator
   const int ew = tc_epi_warps(), ew0 = nwarp - ew;
   const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem);
   __shared__ int s_fail, s_efail;
@@ -376,12 +402,12 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
     auto coords = [&](long long g, int& ti, int& tj, int& c) {
       const long long k = g / nk;
       c = (int)(g - k * nk);
-      tc_tile(t_begin + k * t_step, n, ti, tj);
+      tc_tile<NB>(t_begin + k * t_step, n, ti, tj);
     };
     for (long long g = 0; g < total && g < TC_PREF; ++g) {  // the first chunks
       int ti, tj, c;
       coords(g, ti, tj, c);
-      tc_issue_copy(st, (int)g, s0 + (unsigned)g * TC_BUF, imgA, imgB, ti, tj, c, nk);
+      tc_issue_copy<NB>(st, (int)g, s0 + (unsigned)g * BUF, imgA, imgB, ti, tj, c, nk);
     }
     for (long long g = 0; g < total && ok; ++g) {
       const int bf = (int)(g % TC_NBUF);
@@ -393,12 +419,12 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
         ok = tc_wait(st, TC_B_FREE + bn);
         int ti2, tj2, c2;
         coords(gn, ti2, tj2, c2);
-        if (ok) tc_issue_copy(st, bn, s0 + (unsigned)bn * TC_BUF, imgA, imgB, ti2, tj2, c2, nk);
+        if (ok) tc_issue_copy<NB>(st, bn, s0 + (unsigned)bn * BUF, imgA, imgB, ti2, tj2, c2, nk);
       }
       if (ok) ok = tc_wait(st, TC_B_LOAD + bf);
       // the epilogue has read this accumulator's previous tile (of this call or an earlier one)
       if (ok && cc == 0) ok = tc_wait(st, TC_B_EMPTY + acc);
-      if (ok) tc_issue_mma(st, bf, s0 + (unsigned)bf * TC_BUF, st.tmem + 128u * acc, cc == 0, cc == nk - 1, acc);
+      if (ok) tc_issue_mma<NB>(st, bf, s0 + (unsigned)bf * BUF, st.tmem + ACC * acc, cc == 0, cc == nk - 1, acc);
     }
     // no copy or MMA still reads the buffers, and every read-back arrival is
     // consumed, so that the barrier phases of the next call start in step
@@ -406,29 +432,28 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
     if (ok) ok = tc_wait(st, TC_B_EMPTY) && tc_wait(st, TC_B_EMPTY + 1);
     if (!ok) s_fail = 1;
   } else if (warp >= ew0) {
-    // ---- epilogue: per half tile (32 columns of both planes) the warps copy
+    // ---- epilogue: per part (16 columns of both planes) the warps copy
     //      their lane quadrant's accumulator rows into the stage, then all
     //      epilogue threads add the stage into W_lo with row-contiguous accesses
     const int et = tid - ew0 * 32, ethreads = ew * 32;
-    const int quad = warp & 3, wpq = ew / 4, part = (warp - ew0) >> 2;
-    const int cpw = 32 / wpq;                          // columns of a half per warp
-    const int ipt = TC_M * 8 / ethreads;               // float4 items per thread and plane: 4 or 8
-    float* stage = reinterpret_cast<float*>(smem + TC_SMEM);  // [2 planes][128 rows][TC_SLD]
+    const int quad = warp & 3, wpq = ew / 4, pl0 = (warp - ew0) >> 2;  // wpq = 2: one plane per warp
+    const int ipt = TC_M * (TC_PC / 4) / ethreads;  // float4 items per thread and plane: 2 or 4
+    float4* stage = reinterpret_cast<float4*>(smem + TC_NBUF * BUF);  // [2 planes][128 rows][4 slots]
     const unsigned lane_base = (unsigned)(32 * quad) << 16;
     bool ok = true;
     for (long long k = 0; k < my_tiles && ok; ++k) {
       int ti, tj;
-      tc_tile(t_begin + k * t_step, n, ti, tj);
-      const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * TC_N;
-      for (int h = 0; h < 2 && ok; ++h) {
-        // this half of W_lo, read before the accumulator is waited for
-        float4 wr[8], wi[8];
-        int okv[8];
+      tc_tile<NB>(t_begin + k * t_step, n, ti, tj);
+      const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * TC_N * NB;
+      for (int h = 0; h < 4 * NB && ok; ++h) {  // 16-column parts of the tile
+        // this part of W_lo, read before the accumulator is waited for
+        float4 wr[4], wi[4];
+        int okv[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           okv[u] = 0;
           if (u >= ipt) continue;
-          const int it = et + u * ethreads, row = it >> 3, gi = i0 + row, gj = j0 + 32 * h + (it & 7) * 4;
+          const int it = et + u * ethreads, gi = i0 + (it >> 2), gj = j0 + TC_PC * h + (it & 3) * 4;
           okv[u] = gi < n ? (gj + 4 <= n ? 2 : (gj < n ? 1 : 0)) : 0;
           if (okv[u] == 2) {
             const size_t o = (size_t)gi * a.ldl + gj;
@@ -447,21 +472,19 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
             break;
           }
         }
-        // accumulator rows of this warp's quadrant -> stage
+        // accumulator rows of this warp's quadrant -> stage (Dr at column 0 of the
+        // 64-row block h / 4, Di 64 further)
         const int row = 32 * quad + lane;
-        for (int c16 = 0; c16 < cpw; c16 += 16) {
-          const int cc = part * cpw + c16;  // column within the half
-          float dr[16], di[16];
-          const unsigned addr = st.tmem + lane_base + 128u * acc + (unsigned)(32 * h + cc);
-          tc_ld16(addr, dr);
-          tc_ld16(addr + TC_N, di);
+        const unsigned addr = st.tmem + lane_base + ACC * acc + 128u * (h >> 2) + (unsigned)(TC_PC * (h & 3));
+        for (int pl = pl0; pl < 2; pl += wpq) {
+          float v[16];
+          tc_ld16(addr + TC_N * pl, v);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            stage[(0 * TC_M + row) * TC_SLD + cc + q] = dr[q];
-            stage[(1 * TC_M + row) * TC_SLD + cc + q] = di[q];
-          }
+          for (int q4 = 0; q4 < 4; ++q4)
+            stage[pl * TC_M * 4 + tc_stage_slot(row, q4)] =
+                make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
         }
-        if (h == 1) {  // this warp has read accumulator acc: one arrival per warp
+        if (h == 4 * NB - 1) {  // this warp has read accumulator acc: one arrival per warp
           asm volatile("tcgen05.fence::before_thread_sync;");
           __syncwarp();
           if (lane == 0)
@@ -469,23 +492,23 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
         }
         asm volatile("bar.sync 1, %0;" ::"r"(ethreads) : "memory");  // stage complete
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           if (!okv[u]) continue;
-          const int it = et + u * ethreads, rw = it >> 3, c4 = (it & 7) * 4;
-          const int gi = i0 + rw, gj = j0 + 32 * h + c4;
-          const float* sr = stage + (0 * TC_M + rw) * TC_SLD + c4;
-          const float* si = stage + (1 * TC_M + rw) * TC_SLD + c4;
+          const int it = et + u * ethreads, rw = it >> 2, q4 = it & 3;
+          const int gi = i0 + rw, gj = j0 + TC_PC * h + 4 * q4;
+          const float4 sr = stage[tc_stage_slot(rw, q4)], si = stage[TC_M * 4 + tc_stage_slot(rw, q4)];
           const size_t o = (size_t)gi * a.ldl + gj;
           if (okv[u] == 2) {
             float4 x = wr[u], y = wi[u];
-            x.x += sr[0]; x.y += sr[1]; x.z += sr[2]; x.w += sr[3];
-            y.x += si[0]; y.y += si[1]; y.z += si[2]; y.w += si[3];
+            x.x += sr.x; x.y += sr.y; x.z += sr.z; x.w += sr.w;
+            y.x += si.x; y.y += si.y; y.z += si.z; y.w += si.w;
             *reinterpret_cast<float4*>(a.Wr + o) = x;
             *reinterpret_cast<float4*>(a.Wi + o) = y;
           } else {
+            const float srv[4] = {sr.x, sr.y, sr.z, sr.w}, siv[4] = {si.x, si.y, si.z, si.w};
             for (int q = 0; q < 4 && gj + q < n; ++q) {
-              a.Wr[o + q] += sr[q];
-              a.Wi[o + q] += si[q];
+              a.Wr[o + q] += srv[q];
+              a.Wi[o + q] += siv[q];
             }
           }
         }
@@ -501,7 +524,7 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
 // bytes of the global operand images for a region of n pixels and r <= R delayed columns
 __host__ __device__ __forceinline__ size_t tc_image_bytes(int n, int R) {
   const size_t nk = (size_t)(R + TC_KC - 1) / TC_KC;
-  const size_t nI = (size_t)(n + TC_M - 1) / TC_M, nJ = (size_t)(n + TC_N - 1) / TC_N;
+  const size_t nI = (size_t)(n + TC_M - 1) / TC_M, nJ = (size_t)tc_nj64(n);
   return nI * nk * TC_ACHUNK + nJ * nk * TC_BCHUNK;
 }
 

@@ -58,6 +58,8 @@ constexpr long long kNoCand = (long long)kKeyMask;                 // above ever
 constexpr unsigned kSeqMask = (1u << (64 - kSeqShift)) - 1;
 // FP64 own state at the start of the dynamic shared memory: T'[kMaxPorts], diag, e, dv, 1/dv, |dv|^2
 constexpr size_t kOwnStateSmem = (size_t)(kMaxPorts + 4) * kOwnMax * sizeof(c128) + kOwnMax * sizeof(double);
+constexpr size_t kXsBytes = (size_t)kMaxDelay * kOwnMax * sizeof(float2);  // delayed columns of the own pixels
+constexpr size_t kPartBytes = (size_t)16 * kOwnMax * sizeof(float2);       // U2 partial sums
 static_assert(kOwnStateSmem % 1024 == 0, "fold operands stay 1024-B aligned");
 
 // a CTA's candidate of one round, with everything the other CTAs need to keep it
@@ -123,7 +125,6 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ int s_pos[kOwnMax];
   __shared__ unsigned char s_b[kOwnMax];
   __shared__ float2 s_wk[kOwnMax];
-  __shared__ float2 s_part[16 * kOwnMax];        // partial delayed sums (U2)
   __shared__ c128 s_c[kOwnMax], s_ac[kOwnMax];  // column entry c_j and alpha c_j of the kept flip
   __shared__ float2 s_beta[kMaxDelay], s_alpha[kMaxDelay];
   __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
@@ -135,6 +136,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   __shared__ int s_fail, s_bad;
   // delayed columns of the own pixels between folds, column-major: Xs[i * OS + jl] = x_i[pb + jl]
   float2* Xs = reinterpret_cast<float2*>(work);
+  // partial delayed sums of the update (U2), after the largest Xs; dead during a fold
+  float2* s_part = reinterpret_cast<float2*>(work + kXsBytes);
   const int OS = (own + 31) & ~31;
   const int R = a.R;
   int r = ctl->r_delay;
@@ -219,11 +222,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     load_pos();
     return true;
   };
-  // tensor-core fold: warp 0 holds TC_TMEM_COLS columns of tensor memory for the whole search
+  // tensor-core fold (tiles of 128 x 128): warp 0 holds all 512 columns of tensor memory for the whole search
   __shared__ __align__(8) unsigned long long s_tc_bars[TC_NBAR];
   __shared__ unsigned s_tmem;
   TcState tcs{};
-  if (a.tensor_fold) tc_setup(tcs, s_tc_bars, &s_tmem);
+  if (a.tensor_fold) tc_setup(tcs, s_tc_bars, &s_tmem, tc_tmem_cols(2));
   // the fold reuses the shared memory of the delayed rows: they are in global
   // X as well and the delayed set is empty afterwards
   auto flush = [&]() -> bool {
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
                  (long long)gridDim.x * blockDim.x);
       if (!grid_sync(ctl)) return false;
       tick(14);
-      if (!tc_fold_tiles(a, r, a.tcimgA, a.tcimgB, work, tcs, blockIdx.x, gridDim.x)) {
+      if (!tc_fold_tiles<2>(a, r, a.tcimgA, a.tcimgB, work, tcs, blockIdx.x, gridDim.x)) {
         if (threadIdx.x == 0) latch_status(ctl, PNGF_ETIMEOUT);
         return false;
       }
@@ -683,11 +686,16 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
-constexpr size_t kMixedWork = kFlushSmem > (size_t)TC_FOLD_SMEM ? kFlushSmem : (size_t)TC_FOLD_SMEM;
+constexpr size_t cmax(size_t x, size_t y) { return x > y ? x : y; }
+constexpr size_t kMixedWork = cmax(cmax(kFlushSmem, kXsBytes + kPartBytes), (size_t)tc_fold_smem(2));
 static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
 static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
 static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
 constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
+// dynamic + static (under 14 KB) shared memory stays within the 196 KB
+// carve-out, less the 1 KB a block reserves: the remaining 60 KB of L1 hold the
+// kernel's local-memory spills and its global reads
+static_assert(kMixedSmem + 14 * 1024 <= 195 * 1024, "mixed kernel shared memory");
 
 static void* mixed_kernel_for(int objective) {
   return objective == PNGF_OBJ_MAX_WEIGHTED_POWER ? (void*)dbs_mixed_kernel<PNGF_OBJ_MAX_WEIGHTED_POWER>
