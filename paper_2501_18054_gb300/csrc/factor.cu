@@ -363,6 +363,17 @@ __global__ void gsum_kernel(const c128* __restrict__ G, long long nn, double* __
   }
 }
 
+// G as unevaluated sums of two FP32 values per real part, hi = fl32(g) and
+// lo = fl32(g - hi) (48 significant bits), for the double-float refresh
+// residual of the mixed search
+__global__ void gsplit_kernel(const c128* __restrict__ G, long long nn, float4* __restrict__ G2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const c128 g = G[i];
+    const float rh = (float)g.x, ih = (float)g.y;
+    G2[i] = make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- driver
@@ -385,6 +396,8 @@ pngf_status factor_fp64(pngf_ctx* c, const uint8_t* b) {
     build_system<<<grid, 256, 0, s>>>(c->G, c->dv, b, n, ldw, LU, v, bb);
   }
   gsum_kernel<<<c->n_sm * 4, 256, 0, s>>>(c->G, (long long)n * n, at<double>(c, c->L.gsum));
+  if (c->cfg.precision == PNGF_MIXED)
+    gsplit_kernel<<<c->n_sm * 4, 256, 0, s>>>(c->G, (long long)n * n, at<float4>(c, c->L.gsplit));
   // LU with partial pivoting
   for (int j0 = 0; j0 < n; j0 += NB) {
     int jb = n - j0 < NB ? n - j0 : NB;

@@ -1,0 +1,219 @@
+// Double-float refresh of the mixed search (R0 and R1 of the iterative
+// refinement): x = v.[e, T] at the active pixels as FP32 pairs, and the
+// residuals r = rhs - y + G x of the own rows with x2 = v.r.
+#pragma once
+#include "sweep_common.cuh"
+
+namespace pngf {
+namespace {
+
+// ---------------------------------------------------------------- double-float refresh (mixed search)
+// An SM of this GPU retires about 1.7 FP64 FMA lanes per clock against 128
+// FP32 lanes, so the mixed search forms the residual of R1 in double-float
+// arithmetic: a real number is the unevaluated sum hi + lo of two FP32 values
+// (48 significant bits).
+//  - product of two pairs: hi_a hi_b = p + err exactly, with p = fl(hi_a hi_b)
+//    and err = fma(hi_a, hi_b, -p) (Dekker's exact product in its fused
+//    multiply-add form); the cross terms hi_a lo_b + lo_a hi_b are formed in
+//    FP32, lo_a lo_b (2^-48 relative) is dropped;
+//  - sum: Knuth's TwoSum adds p to the running hi and keeps the rounding error
+//    exactly; rounding errors and cross terms gather in lo.
+// A lane's sum over k terms then errs by about k 2^-48 sum_i |G_ji x_i|, next
+// to k 2^-53 for the FP64 sum and far below the FP32 drift the refresh
+// removes.  Round-to-nearest intrinsics throughout keep the compiler from
+// contracting a product and a sum into one FMA, which would break the exact
+// transformations.
+struct dfsum {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_madd(dfsum& s, float a1, float a2, float b1, float b2) {
+  const float p = __fmul_rn(a1, b1);
+  const float err = __fmaf_rn(a1, b1, -p);
+  const float cross = __fmaf_rn(a1, b2, __fmaf_rn(a2, b1, err));
+  const float t = __fadd_rn(s.hi, p);
+  const float bv = __fsub_rn(t, s.hi);
+  const float rnd = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(rnd, cross));
+}
+__device__ __forceinline__ double df_value(dfsum s) { return (double)s.hi + (double)s.lo; }
+// (Re hi, Re lo, Im hi, Im lo) of an FP64 complex number
+__device__ __forceinline__ float4 df_split(c128 x) {
+  const float rh = (float)x.x, ih = (float)x.y;
+  return make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+}
+
+// R0, mixed search: x = v.[e, T] at this CTA's active pixels (act, m: the
+// active list in shared memory), as FP32 pairs at the pixel's rank t in the
+// list, xs[q n + t]
+template <int NV>
+__device__ void refresh_x_df_t(const SweepArgs& a, int pb, int pe, const int* act, int m) {
+  const int t0 = count_below(act, m, pb), t1 = count_below(act, m, pe);
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const int j = act[t];
+    const c128 vj = a.v[j];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
+      a.xs[(size_t)q * a.n + t] = df_split(cmul(vj, y));
+    }
+  }
+}
+
+__device__ __forceinline__ void df_add(dfsum& s, float hi, float lo) {
+  const float t = __fadd_rn(s.hi, hi);
+  const float bv = __fsub_rn(t, s.hi);
+  const float rnd = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bv)), __fsub_rn(hi, bv));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(rnd, lo));
+}
+
+__device__ void refresh_x_df(const SweepArgs& a, int pb, int pe, const int* act, int m) {
+  switch (a.n_o) {
+    case 1: refresh_x_df_t<2>(a, pb, pe, act, m); break;
+    case 2: refresh_x_df_t<3>(a, pb, pe, act, m); break;
+    case 3: refresh_x_df_t<4>(a, pb, pe, act, m); break;
+    case 4: refresh_x_df_t<5>(a, pb, pe, act, m); break;
+    case 5: refresh_x_df_t<6>(a, pb, pe, act, m); break;
+    case 6: refresh_x_df_t<7>(a, pb, pe, act, m); break;
+    case 7: refresh_x_df_t<8>(a, pb, pe, act, m); break;
+    default: refresh_x_df_t<9>(a, pb, pe, act, m); break;
+  }
+}
+
+// R1, mixed search: residuals of own rows over the active columns in
+// double-float products (G2: G as FP32 pairs).
+//
+// G is symmetric, so row j at the active columns is read as the entries
+// G[i][j], j in [pb, pe), of the active rows i.  Thread jl of a group of gs
+// threads (own rows rounded up to a warp) takes own row pb + jl (lanes past
+// the own rows repeat the last one); the ng = blockDim / gs groups take the
+// active list in turn.  A stage is S = ng R consecutive list entries, R per
+// group, and the operands travel by asynchronous 16-byte copies into a ring
+// of RD_D stages: every thread copies the G entries it multiplies itself, and
+// every warp the x entries of its group's rows (x: NV x R float4 per warp and
+// stage).  A thread therefore waits only for its own copies (cp.async groups,
+// one per stage) and a warp-level barrier, and the warps run through the
+// ring independently, RD_D - 1 stages in flight.
+//
+// The groups' partial sums are then added in shared memory, one vector at a
+// time and in group order, and r and x2 = v.r are formed in FP64.
+//
+// area, area_bytes: 16-byte aligned shared memory for the ring (the partial
+// sums reuse it: blockDim float4).
+constexpr int RD_D = 4;
+constexpr int RD_RMAX = 8;
+// list entries per group and stage for own rows and NV vectors in area_bytes (0: too small)
+__host__ __device__ __forceinline__ int rd_rows(int own, int NV, int nthreads, unsigned area_bytes) {
+  const int gs = (own + 31) & ~31, ng = nthreads / gs;
+  const unsigned per_r = (unsigned)(ng * gs) * 16u + (unsigned)(nthreads / 32) * (unsigned)NV * 16u;
+  const int R = (int)(area_bytes / ((unsigned)RD_D * per_r));
+  return R < RD_RMAX ? R : RD_RMAX;
+}
+
+template <int NV>
+__device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, int pe, const int* act, int m,
+                                                   unsigned char* area, unsigned area_bytes) {
+  const int own = pe - pb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)blockDim.x >> 5;
+  const int gs = (own + 31) & ~31, ng = (int)blockDim.x / gs;  // own <= blockDim
+  const int grp = tid / gs, jl = tid - grp * gs, jc = min(jl, own - 1);
+  const int R = rd_rows(own, NV, (int)blockDim.x, area_bytes);  // >= 1: checked by the host
+  const int S = ng * R;
+  // a stage: G entries [ng R][gs] float4 (group g's rows at g R), then x [nw][NV][R] float4
+  const unsigned stage = (unsigned)(S * gs) * 16u + (unsigned)(nw * NV * R) * 16u;
+  const unsigned oX = (unsigned)(S * gs) * 16u;
+  const int nst = (m + S - 1) / S;
+  const unsigned s0 = (unsigned)__cvta_generic_to_shared(area);
+  const bool live = grp < ng;
+  // this thread's copies of stage k into slot k % RD_D (always one cp.async group)
+  auto issue = [&](int k) {
+    if (live && k < nst) {
+      const unsigned dst = s0 + (unsigned)(k % RD_D) * stage;
+      for (int r = 0; r < R; ++r) {
+        const int t = k * S + grp + ng * r;
+        if (t >= m) break;
+        const float4* src = a.G2 + (size_t)act[t] * a.n + pb + jc;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (unsigned)((grp * R + r) * gs + jl) * 16u),
+                     "l"(src)
+                     : "memory");
+      }
+      for (int e = lane; e < NV * R; e += 32) {
+        const int q = e / R, r = e - q * R, t = k * S + grp + ng * r;
+        if (t < m)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + oX + (unsigned)((warp * NV + q) * R + r) * 16u),
+                       "l"(a.xs + (size_t)q * a.n + t)
+                       : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // earlier use of this shared memory (the active list's neighbours, the delayed set) is complete
+  __syncthreads();
+  for (int k = 0; k < RD_D - 1; ++k) issue(k);
+  dfsum sr[NV], si[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sr[q] = si[q] = dfsum{0.f, 0.f};
+  for (int k = 0; k < nst; ++k) {
+    __syncwarp();  // this warp is done with slot (k - 1) % RD_D, which stage k + RD_D - 1 refills
+    issue(k + RD_D - 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(RD_D - 1) : "memory");  // stage k has landed
+    __syncwarp();                                                         // ... for every lane of the warp
+    if (!live) continue;
+    const unsigned char* st = area + (size_t)(k % RD_D) * stage;
+    const float4* gst = reinterpret_cast<const float4*>(st) + grp * R * gs + jl;
+    const float4* xst = reinterpret_cast<const float4*>(st + oX) + warp * NV * R;
+    for (int r = 0; r < R; ++r) {
+      if (k * S + grp + ng * r >= m) break;
+      const float4 gg = gst[r * gs];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float4 x = xst[q * R + r];
+        df_madd(sr[q], gg.x, gg.y, x.x, x.y);    // Re G Re x
+        df_madd(sr[q], -gg.z, -gg.w, x.z, x.w);  // - Im G Im x
+        df_madd(si[q], gg.x, gg.y, x.z, x.w);    // Re G Im x
+        df_madd(si[q], gg.z, gg.w, x.x, x.y);    // Im G Re x
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  float4* part = reinterpret_cast<float4*>(area);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (live) part[tid] = make_float4(sr[q].hi, sr[q].lo, si[q].hi, si[q].lo);
+    __syncthreads();
+    if (tid < own) {
+      dfsum re{0.f, 0.f}, im{0.f, 0.f};
+      for (int g2 = 0; g2 < ng; ++g2) {
+        const float4 p = part[g2 * gs + tid];
+        df_add(re, p.x, p.y);
+        df_add(im, p.z, p.w);
+      }
+      const int j = pb + tid;
+      const c128 rhs = q == 0 ? a.cd[j] : a.God[(size_t)(q - 1) * a.n + j];
+      const c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
+      const c128 r = cadd(csub(rhs, y), mk(df_value(re), df_value(im)));
+      rvec(a, 0, q)[j] = r;
+      const c128 x2 = cmul(a.v[j], r);
+      x2f(a, q)[j] = make_float2((float)x2.x, (float)x2.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void refresh_residual_df(const SweepArgs& a, int pb, int pe, const int* act, int m, unsigned char* area,
+                                    unsigned area_bytes) {
+  switch (a.n_o) {
+    case 1: refresh_residual_df_t<2>(a, pb, pe, act, m, area, area_bytes); break;
+    case 2: refresh_residual_df_t<3>(a, pb, pe, act, m, area, area_bytes); break;
+    case 3: refresh_residual_df_t<4>(a, pb, pe, act, m, area, area_bytes); break;
+    case 4: refresh_residual_df_t<5>(a, pb, pe, act, m, area, area_bytes); break;
+    case 5: refresh_residual_df_t<6>(a, pb, pe, act, m, area, area_bytes); break;
+    case 6: refresh_residual_df_t<7>(a, pb, pe, act, m, area, area_bytes); break;
+    case 7: refresh_residual_df_t<8>(a, pb, pe, act, m, area, area_bytes); break;
+    default: refresh_residual_df_t<9>(a, pb, pe, act, m, area, area_bytes); break;
+  }
+}
+
+}  // namespace
+}  // namespace pngf

@@ -50,6 +50,8 @@ struct SweepArgs {
   void* rec;  // [2][P] candidate records
   unsigned long long* slots;  // [2][P] round words of the mixed search, 128 B apart
   int* actg;                  // n: active-pixel list of the last refresh (written by CTA 0)
+  const float4* G2;           // n x n: G as FP32 pairs (Re hi, Re lo, Im hi, Im lo)
+  float4* xs;                 // (1 + n_o) x n: x = v.[e, T] at the active pixels, as FP32 pairs
 };
 
 // a CTA's candidate of one scoring round, with the state the pivot needs
@@ -919,6 +921,8 @@ SweepArgs make_args(pngf_ctx* c) {
   a.rec = c->ws + L.rec;
   a.slots = at<unsigned long long>(c, L.slots);
   a.actg = at<int>(c, L.actg);
+  a.G2 = a.mixed ? at<float4>(c, L.gsplit) : nullptr;
+  a.xs = a.mixed ? at<float4>(c, L.xs) : nullptr;
   a.tensor_fold = c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold;
   a.tcimgA = reinterpret_cast<unsigned char*>(c->ws) + L.tcimg;
   a.tcimgB = a.tcimgA + L.tcimgA_bytes;

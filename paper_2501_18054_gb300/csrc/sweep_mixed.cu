@@ -21,6 +21,7 @@
 #include <cstdio>
 
 #include "flush_tc.cuh"
+#include "refresh_df.cuh"
 
 namespace pngf {
 namespace {
@@ -60,6 +61,19 @@ constexpr unsigned kSeqMask = (1u << (64 - kSeqShift)) - 1;
 constexpr size_t kOwnStateSmem = (size_t)(kMaxPorts + 4) * kOwnMax * sizeof(c128) + kOwnMax * sizeof(double);
 constexpr size_t kXsBytes = (size_t)kMaxDelay * kOwnMax * sizeof(float2);  // delayed columns of the own pixels
 constexpr size_t kPartBytes = (size_t)16 * kOwnMax * sizeof(float2);       // U2 partial sums
+constexpr size_t cmax(size_t x, size_t y) { return x > y ? x : y; }
+constexpr size_t kMixedWork = cmax(cmax(kFlushSmem, kXsBytes + kPartBytes), (size_t)tc_fold_smem(2));
+static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
+static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
+static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
+constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
+// dynamic + static (under 14 KB) shared memory stays within the 196 KB
+// carve-out, less the 1 KB a block reserves: the remaining 60 KB of L1 hold the
+// kernel's local-memory spills and its global reads
+static_assert(kMixedSmem + 14 * 1024 <= 195 * 1024, "mixed kernel shared memory");
+// a refresh holds the active list (n ints) and then the residual's copy ring
+// (its partial sums, kThreads float4, reuse the ring) in the work area
+__host__ __device__ constexpr size_t rd_list_bytes(int n) { return ((size_t)n * 4 + 15) / 16 * 16; }
 static_assert(kOwnStateSmem % 1024 == 0, "fold operands stay 1024-B aligned");
 
 // a CTA's candidate of one round, with everything the other CTAs need to keep it
@@ -538,13 +552,18 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         ++n_refresh;
         store_et(false);
         __syncthreads();
-        refresh_x(a, pb, pe);
-        if (!grid_sync(ctl)) { failed = true; break; }
-        tick(8);
         // the delayed set is empty here: its shared memory holds the active-pixel
         // list, then the staging of the correction
-        const int m_act = refresh_residual(a, pb, pe, reinterpret_cast<int*>(work));
-        const int t_end = count_below(reinterpret_cast<const int*>(work), m_act, pe - 1);
+        int* act = reinterpret_cast<int*>(work);
+        const int m_act = active_list(a, act);
+        if (cta == 0)  // for the correction, after the next grid barrier
+          for (int q = tid; q < m_act; q += blockDim.x) a.actg[q] = act[q];
+        refresh_x_df(a, pb, pe, act, m_act);
+        if (!grid_sync(ctl)) { failed = true; break; }
+        tick(8);
+        // the residual's copy ring after the list
+        refresh_residual_df(a, pb, pe, act, m_act, work + rd_list_bytes(n), (unsigned)(kMixedWork - rd_list_bytes(n)));
+        const int t_end = count_below(act, m_act, pe - 1);
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(9);
         correct_strips<true>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(work),
@@ -686,16 +705,6 @@ pngf_status mixed_after_factor(pngf_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
-constexpr size_t cmax(size_t x, size_t y) { return x > y ? x : y; }
-constexpr size_t kMixedWork = cmax(cmax(kFlushSmem, kXsBytes + kPartBytes), (size_t)tc_fold_smem(2));
-static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
-static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
-static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
-constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
-// dynamic + static (under 14 KB) shared memory stays within the 196 KB
-// carve-out, less the 1 KB a block reserves: the remaining 60 KB of L1 hold the
-// kernel's local-memory spills and its global reads
-static_assert(kMixedSmem + 14 * 1024 <= 195 * 1024, "mixed kernel shared memory");
 
 static void* mixed_kernel_for(int objective) {
   return objective == PNGF_OBJ_MAX_WEIGHTED_POWER ? (void*)dbs_mixed_kernel<PNGF_OBJ_MAX_WEIGHTED_POWER>
@@ -734,6 +743,13 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   Control* ctl = a.ctl;
   int grid = mixed_grid(c);
   if ((c->cfg.n_d + grid - 1) / grid > kOwnMax) return PNGF_EINVAL;  // own-pixel state is shared memory
+  {  // the refresh residual's copy ring takes one list entry per group and stage at least, after the active list
+    const int own = (c->cfg.n_d + grid - 1) / grid;
+    const size_t list = rd_list_bytes(c->cfg.n_d);
+    if (list + (size_t)kThreads * 16 > kMixedWork ||
+        rd_rows(own, 1 + c->cfg.n_o, kThreads, (unsigned)(kMixedWork - list)) < 1)
+      return PNGF_EINVAL;
+  }
   cudaError_t err = cudaMemsetAsync(&ctl->bar_count, 0, 2 * sizeof(unsigned), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
   err = cudaMemsetAsync(a.slots, 0, (size_t)2 * grid * kSlotStride * sizeof(unsigned long long), c->stream);
