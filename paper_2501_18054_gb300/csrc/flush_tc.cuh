@@ -353,6 +353,17 @@ __device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf,
   }
 }
 
+// relaxed device-scope reductions W += v (16-byte aligned for the vector form);
+// they are ordered before the grid barrier that ends the fold by its release fence
+__device__ __forceinline__ void tc_red4(float* w, float4 v) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(w), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void tc_red1(float* w, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(w), "f"(v) : "memory");
+}
+
 // 16 consecutive accumulator columns of this thread's lane (tensor-memory lane
 // quadrant of the warp), as floats
 __device__ __forceinline__ void tc_ld16(unsigned addr, float v[16]) {
@@ -372,9 +383,9 @@ __device__ __forceinline__ void tc_ld16(unsigned addr, float v[16]) {
 //     buffers across tile boundaries; the MMAs of a tile go to accumulator
 //     k & 1 once the epilogue has read that accumulator's previous tile;
 //   epilogue (the last tc_epi_warps() warps, named barrier 1): per 16-column
-//     part its threads read their part of W_lo while the tile's MMAs run, copy the
-//     accumulator rows of their lane quadrants (tcgen05.ld) into a shared stage
-//     and add the stage into W_lo with row-contiguous accesses;
+//     part its threads copy the accumulator rows of their lane quadrants
+//     (tcgen05.ld) into a shared stage and add the stage into W_lo with
+//     row-contiguous vector reductions;
 //   the other warps wait at the final barrier.
 // smem: tc_fold_smem(NB) bytes (operand buffers, then the stage).  Returns false
 // after a timeout (the caller then calls tc_teardown with failed = true).
@@ -434,7 +445,7 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
   } else if (warp >= ew0) {
     // ---- epilogue: per part (16 columns of both planes) the warps copy
     //      their lane quadrant's accumulator rows into the stage, then all
-    //      epilogue threads add the stage into W_lo with row-contiguous accesses
+    //      epilogue threads add the stage into W_lo with row-contiguous reductions
     const int et = tid - ew0 * 32, ethreads = ew * 32;
     const int quad = warp & 3, wpq = ew / 4, pl0 = (warp - ew0) >> 2;  // wpq = 2: one plane per warp
     const int ipt = TC_M * (TC_PC / 4) / ethreads;  // float4 items per thread and plane: 2 or 4
@@ -446,8 +457,7 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
       tc_tile<NB>(t_begin + k * t_step, n, ti, tj);
       const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * TC_N * NB;
       for (int h = 0; h < 4 * NB && ok; ++h) {  // 16-column parts of the tile
-        // this part of W_lo, read before the accumulator is waited for
-        float4 wr[4], wi[4];
+        // which of this thread's four-column items of the part lie inside W (2: all four, 1: some)
         int okv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -455,11 +465,6 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
           if (u >= ipt) continue;
           const int it = et + u * ethreads, gi = i0 + (it >> 2), gj = j0 + TC_PC * h + (it & 3) * 4;
           okv[u] = gi < n ? (gj + 4 <= n ? 2 : (gj < n ? 1 : 0)) : 0;
-          if (okv[u] == 2) {
-            const size_t o = (size_t)gi * a.ldl + gj;
-            wr[u] = *reinterpret_cast<const float4*>(a.Wr + o);
-            wi[u] = *reinterpret_cast<const float4*>(a.Wi + o);
-          }
         }
         if (h == 0) {
           // the decision to stop is taken by all epilogue threads together, so that
@@ -498,17 +503,17 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
           const int gi = i0 + rw, gj = j0 + TC_PC * h + 4 * q4;
           const float4 sr = stage[tc_stage_slot(rw, q4)], si = stage[TC_M * 4 + tc_stage_slot(rw, q4)];
           const size_t o = (size_t)gi * a.ldl + gj;
+          // W_lo += stage as reductions performed in L2: no read on this side, so
+          // the epilogue never waits for memory; one writer per element and fold,
+          // one FP32 rounding per element as a load-add-store
           if (okv[u] == 2) {
-            float4 x = wr[u], y = wi[u];
-            x.x += sr.x; x.y += sr.y; x.z += sr.z; x.w += sr.w;
-            y.x += si.x; y.y += si.y; y.z += si.z; y.w += si.w;
-            *reinterpret_cast<float4*>(a.Wr + o) = x;
-            *reinterpret_cast<float4*>(a.Wi + o) = y;
+            tc_red4(a.Wr + o, sr);
+            tc_red4(a.Wi + o, si);
           } else {
             const float srv[4] = {sr.x, sr.y, sr.z, sr.w}, siv[4] = {si.x, si.y, si.z, si.w};
             for (int q = 0; q < 4 && gj + q < n; ++q) {
-              a.Wr[o + q] += srv[q];
-              a.Wi[o + q] += siv[q];
+              tc_red1(a.Wr + o + q, srv[q]);
+              tc_red1(a.Wi + o + q, siv[q]);
             }
           }
         }
