@@ -520,12 +520,14 @@ def main():
     else:
         # dominant kernel: the persistent mixed DBS sweep.  Algorithmic HBM bytes per
         # launch: per flush the upper triangle of the two FP32 planes read + written
-        # (16 B per element), per refresh one read of G (16 B) and of the FP32
-        # upper triangle (8 B), per kept flip one column of the FP32 planes (8 B x n),
-        # per evaluation (3 + n_o) x 16 B of FP64 state.
-        n_flush, n_ref = int(c2[:, 5].sum()), int(c2[:, 4].sum())
-        bytes_alg = (n_flush * 16.0 * tri + n_ref * (16.0 * n * n + 8.0 * tri) + acc_per_step * 8.0 * n
-                     + evals_per_step * (3 + n_o) * 16.0)
+        # (16 B per element); per refresh with m active pixels the m rows of G as FP32
+        # pairs (16 B x m x n), the FP32 upper triangle (8 B) and its entries in the
+        # active rows above each column strip (8 B x m / n per element); per kept flip
+        # one column of the FP32 planes (8 B x n); per evaluation (3 + n_o) x 16 B of
+        # FP64 state.
+        n_flush, n_ref, sum_m = int(c2[:, 5].sum()), int(c2[:, 4].sum()), float(c2[:, 7].sum())
+        bytes_alg = (n_flush * 16.0 * tri + 16.0 * n * sum_m + n_ref * 8.0 * tri + 8.0 * tri * sum_m / n
+                     + acc_per_step * 8.0 * n + evals_per_step * (3 + n_o) * 16.0)
         gbs = bytes_alg / (step_ms / 1e3) / 1e9
         traffic, traffic_note = None, "no capture of the current kernel sources"
         if args.workload == TRAFFIC_CAPTURE["workload"] and sources_fingerprint() == TRAFFIC_CAPTURE["sources_sha256"]:
@@ -538,8 +540,8 @@ def main():
                     "kernel": "dbs_mixed_kernel",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
                     "note": "each run keeps one flip at a time (a latency-bound chain of word exchange, "
-                            "fetch and FP64 state update per kept flip) and refreshes e, T in FP64 (FP64-pipe "
-                            "bound); see phase_ms_cta0"}
+                            "fetch and FP64 state update per kept flip) and refreshes e, T with a double-float "
+                            "residual (FP32-pipe bound); see phase_ms_cta0"}
     if runs_note:
         roofline["runs"] = runs_note
     # ---- end to end through the C ABI with host buffers (pinned): visiting orders in,

@@ -180,7 +180,8 @@ pngf_status pngf_accept_flip_noalloc(pngf_ctx* ctx, int32_t pixel);
  *   trace_f   double trace_cap (device, out): objective after each kept flip, or NULL
  *   counters  int64 8 (device, out): [0] kept flips, [1] attempted flips
  *             (evaluations in sequential semantics), [2] sweeps run,
- *             [3] converged (0/1), [4] refreshes, [5] flushes, [6] status, [7] 0
+ *             [3] converged (0/1), [4] refreshes, [5] flushes, [6] status,
+ *             [7] active pixels (b_i = 1) summed over the refreshes
  * Kept flips past trace_cap are still applied but not recorded; [6] is then
  * PNGF_ECAPACITY.  The state stays on the device for further calls.
  * Mixed precision keeps each CTA's share of the pixels in shared memory:

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     s_f = ctl->f;
   }
   __syncthreads();
-  long long n_acc = 0, n_evals = 0, n_refresh = 0;
+  long long n_acc = 0, n_evals = 0, n_refresh = 0, sum_active = 0;
   int sweeps_done = 0, converged = 0, status = PNGF_OK;
   // per-phase SM-cycle accounting of CTA 0 (thread 0 sees every phase boundary)
   const bool timer = (cta == 0 && threadIdx.x == 0);
@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(8);
       const int m_act = refresh_residual(a, pb, pe, act_smem);
+      sum_active += m_act;
       const int t_end = count_below(act_smem, m_act, pe - 1);
       if (!grid_sync(ctl)) { failed = true; break; }
       tick(9);
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
     ctl->counters[4] = n_refresh;
     ctl->counters[5] = 0;
     ctl->counters[6] = status;
-    ctl->counters[7] = 0;
+    ctl->counters[7] = sum_active;
     ph[7] = clock64() - t_begin;
     for (int q = 0; q < 16; ++q) ctl->phase_cycles[q] = ph[q];
     if (a.counters)

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   auto load_pos = [&]() {
     for (int jl = tid; jl < own; jl += blockDim.x) s_pos[jl] = a.pos_of[pb + jl];
   };
-  long long n_acc = 0, n_evals = 0, n_refresh = 0, n_flush = 0;
+  long long n_acc = 0, n_evals = 0, n_refresh = 0, n_flush = 0, sum_active = 0;
   int sweeps_done = 0, converged = 0, status = PNGF_OK;
   int since_refresh = ctl->since_refresh;
   int s = 0, t = 0, acc_in_sweep = 0;
@@ -556,6 +556,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         // list, then the staging of the correction
         int* act = reinterpret_cast<int*>(work);
         const int m_act = active_list(a, act);
+        sum_active += m_act;
         if (cta == 0)  // for the correction, after the next grid barrier
           for (int q = tid; q < m_act; q += blockDim.x) a.actg[q] = act[q];
         refresh_x_df(a, pb, pe, act, m_act);
@@ -616,7 +617,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     ctl->counters[4] = n_refresh;
     ctl->counters[5] = n_flush;
     ctl->counters[6] = status;
-    ctl->counters[7] = 0;
+    ctl->counters[7] = sum_active;
     ph[7] = clock64() - t_begin;
     for (int q = 0; q < 16; ++q) ctl->phase_cycles[q] = ph[q];
     if (a.counters)
