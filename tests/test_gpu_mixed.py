@@ -67,6 +67,36 @@ def test_mixed_factor_state_is_fp64(P, fdfd64):
     assert np.max(np.abs(f_gpu - f_ref) / np.abs(f_ref)) < 1e-9
 
 
+@pytest.mark.parametrize("tensor_fold", [0, 1])
+def test_mixed_refresh_restores_fp64_accuracy(P, fdfd64, tensor_fold):
+    """A refresh (the double-float residual r = rhs - M y, then y += W (v r) in
+    FP32) leaves e and T at FP64-level error for the current design, orders of
+    magnitude below the FP32 drift the same kept flips leave without one.
+
+    Best-improvement mode stops after exactly n_sweeps kept flips, and with
+    delay_r = refresh_k = 16 the 16th kept flip is followed by a fold and a
+    refresh, so the state read back is the refreshed one."""
+    case = fdfd64
+    b0 = W.random_design(case.n_d, 5)
+    errs = {}
+    for rk in (16, 0):
+        ctx = _ctx(P, case, mode=P.PNGF_BEST_IMPROVEMENT, tau=1e-9, delay_r=16, refresh_k=rk,
+                   tensor_fold=tensor_fold)
+        ctx.factor(b0)
+        cnt = ctx.dbs_sweep(16)["counters"]
+        assert int(cnt[0]) == 16 and int(cnt[4]) == (1 if rk else 0)
+        b = ctx.design()
+        v = case.dv * b
+        st = ctx.state()
+        e_ref = O.solve_field(case.G_dd, case.c_d, v)
+        T_ref = O.port_projection(case.G_dd, case.G_od, v)
+        errs[rk] = max(rel(st["e"], e_ref), rel(st["T"], T_ref))
+        ctx.close()
+    print("state error after 16 kept flips: refreshed %.3e, not refreshed %.3e" % (errs[16], errs[0]))
+    assert errs[16] < 1e-11
+    assert errs[0] > 100 * errs[16]
+
+
 @pytest.mark.parametrize("n_accepts", [3, 8, 13])
 def test_mixed_accepts_follow_resolves(P, fdfd64, n_accepts):
     """Standalone accepts across a flush (delay_r = 4)."""
