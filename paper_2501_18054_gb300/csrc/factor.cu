@@ -365,12 +365,13 @@ __global__ void gsum_kernel(const c128* __restrict__ G, long long nn, double* __
 
 // G as unevaluated sums of two FP32 values per real part, hi = fl32(g) and
 // lo = fl32(g - hi) (48 significant bits), for the double-float refresh
-// residual of the mixed search
+// residual of the mixed search: (Re hi, Im hi, Re lo, Im lo), so that the
+// (Re, Im) pairs of the hi and of the lo parts are 64-bit operands
 __global__ void gsplit_kernel(const c128* __restrict__ G, long long nn, float4* __restrict__ G2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
     const c128 g = G[i];
     const float rh = (float)g.x, ih = (float)g.y;
-    G2[i] = make_float4(rh, (float)(g.x - (double)rh), ih, (float)(g.y - (double)ih));
+    G2[i] = make_float4(rh, ih, (float)(g.x - (double)rh), (float)(g.y - (double)ih));
   }
 }
 

@@ -37,15 +37,59 @@ __device__ __forceinline__ void df_madd(dfsum& s, float a1, float a2, float b1, 
   s.lo = __fadd_rn(s.lo, __fadd_rn(rnd, cross));
 }
 __device__ __forceinline__ double df_value(dfsum s) { return (double)s.hi + (double)s.lo; }
-// (Re hi, Re lo, Im hi, Im lo) of an FP64 complex number
-__device__ __forceinline__ float4 df_split(c128 x) {
-  const float rh = (float)x.x, ih = (float)x.y;
-  return make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+// ---- packed pairs: two FP32 lanes in one 64-bit operand of the f32x2 instructions
+typedef unsigned long long f2x2;
+__device__ __forceinline__ f2x2 pk2(float lo, float hi) {
+  f2x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2x2 v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2x2 add2(f2x2 a, f2x2 b) {
+  f2x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x2 sub2(f2x2 a, f2x2 b) {
+  f2x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x2 mul2(f2x2 a, f2x2 b) {
+  f2x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x2 fma2(f2x2 a, f2x2 b, f2x2 c) {
+  f2x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// Two double-float multiply-adds in one instruction stream, one per lane of the
+// pairs: (H, L) += (a1 + a2)(b1 + b2) with na1 = -a1 and na2 = -a2 given, so that
+// the exact error of the product comes out negated, -err = fma(-a1, b1, p), and
+// no negation is needed: the same steps as df_madd, with -cross subtracted.
+__device__ __forceinline__ void df_madd2(f2x2& H, f2x2& L, f2x2 a1, f2x2 na1, f2x2 na2, f2x2 b1, f2x2 b2) {
+  const f2x2 p = mul2(a1, b1);
+  const f2x2 nerr = fma2(na1, b1, p);
+  const f2x2 ncross = fma2(na1, b2, fma2(na2, b1, nerr));
+  const f2x2 t = add2(H, p);
+  const f2x2 bv = sub2(t, H);
+  const f2x2 rnd = add2(sub2(H, sub2(t, bv)), sub2(p, bv));
+  H = t;
+  L = add2(L, sub2(rnd, ncross));
+}
+
+// hi and lo FP32 parts of an FP64 value
+__device__ __forceinline__ void df_parts(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
 }
 
 // R0, mixed search: x = v.[e, T] at this CTA's active pixels (act, m: the
 // active list in shared memory), as FP32 pairs at the pixel's rank t in the
-// list, xs[q n + t]
+// list, each part twice so that it is a packed operand as it stands:
+// xs[2 (q n + t)] = (Re hi, Re hi, Re lo, Re lo), xs[2 (q n + t) + 1] the same of Im
 template <int NV>
 __device__ void refresh_x_df_t(const SweepArgs& a, int pb, int pe, const int* act, int m) {
   const int t0 = count_below(act, m, pb), t1 = count_below(act, m, pe);
@@ -55,7 +99,13 @@ __device__ void refresh_x_df_t(const SweepArgs& a, int pb, int pe, const int* ac
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       const c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
-      a.xs[(size_t)q * a.n + t] = df_split(cmul(vj, y));
+      const c128 x = cmul(vj, y);
+      float rh, rl, ih, il;
+      df_parts(x.x, rh, rl);
+      df_parts(x.y, ih, il);
+      float4* dst = a.xs + 2 * ((size_t)q * a.n + t);
+      dst[0] = make_float4(rh, rh, rl, rl);
+      dst[1] = make_float4(ih, ih, il, il);
     }
   }
 }
@@ -82,7 +132,9 @@ __device__ void refresh_x_df(const SweepArgs& a, int pb, int pe, const int* act,
 }
 
 // R1, mixed search: residuals of own rows over the active columns in
-// double-float products (G2: G as FP32 pairs).
+// double-float products (G2: G as FP32 pairs), two real products per packed
+// instruction stream: (Re G Re x, Im G Re x) and (-Im G Im x, Re G Im x) into
+// the (Re, Im) pair of the running sum.
 //
 // G is symmetric, so row j at the active columns is read as the entries
 // G[i][j], j in [pb, pe), of the active rows i.  Thread jl of a group of gs
@@ -91,8 +143,8 @@ __device__ void refresh_x_df(const SweepArgs& a, int pb, int pe, const int* act,
 // active list in turn.  A stage is S = ng R consecutive list entries, R per
 // group, and the operands travel by asynchronous 16-byte copies into a ring
 // of RD_D stages: every thread copies the G entries it multiplies itself, and
-// every warp the x entries of its group's rows (x: NV x R float4 per warp and
-// stage).  A thread therefore waits only for its own copies (cp.async groups,
+// every warp the x entries of its group's rows (x: NV x R x 2 float4 per warp
+// and stage).  A thread therefore waits only for its own copies (cp.async groups,
 // one per stage) and a warp-level barrier, and the warps run through the
 // ring independently, RD_D - 1 stages in flight.
 //
@@ -106,7 +158,7 @@ constexpr int RD_RMAX = 8;
 // list entries per group and stage for own rows and NV vectors in area_bytes (0: too small)
 __host__ __device__ __forceinline__ int rd_rows(int own, int NV, int nthreads, unsigned area_bytes) {
   const int gs = (own + 31) & ~31, ng = nthreads / gs;
-  const unsigned per_r = (unsigned)(ng * gs) * 16u + (unsigned)(nthreads / 32) * (unsigned)NV * 16u;
+  const unsigned per_r = (unsigned)(ng * gs) * 16u + (unsigned)(nthreads / 32) * (unsigned)NV * 32u;
   const int R = (int)(area_bytes / ((unsigned)RD_D * per_r));
   return R < RD_RMAX ? R : RD_RMAX;
 }
@@ -119,8 +171,8 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
   const int grp = tid / gs, jl = tid - grp * gs, jc = min(jl, own - 1);
   const int R = rd_rows(own, NV, (int)blockDim.x, area_bytes);  // >= 1: checked by the host
   const int S = ng * R;
-  // a stage: G entries [ng R][gs] float4 (group g's rows at g R), then x [nw][NV][R] float4
-  const unsigned stage = (unsigned)(S * gs) * 16u + (unsigned)(nw * NV * R) * 16u;
+  // a stage: G entries [ng R][gs] float4 (group g's rows at g R), then x [nw][NV][R][2] float4
+  const unsigned stage = (unsigned)(S * gs) * 16u + (unsigned)(nw * NV * R) * 32u;
   const unsigned oX = (unsigned)(S * gs) * 16u;
   const int nst = (m + S - 1) / S;
   const unsigned s0 = (unsigned)__cvta_generic_to_shared(area);
@@ -137,11 +189,12 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
                      "l"(src)
                      : "memory");
       }
-      for (int e = lane; e < NV * R; e += 32) {
-        const int q = e / R, r = e - q * R, t = k * S + grp + ng * r;
+      for (int e = lane; e < 2 * NV * R; e += 32) {
+        const int h = e & 1, qr = e >> 1, q = qr / R, r = qr - q * R, t = k * S + grp + ng * r;
         if (t < m)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + oX + (unsigned)((warp * NV + q) * R + r) * 16u),
-                       "l"(a.xs + (size_t)q * a.n + t)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                           dst + oX + (unsigned)(((warp * NV + q) * R + r) * 2 + h) * 16u),
+                       "l"(a.xs + 2 * ((size_t)q * a.n + t) + h)
                        : "memory");
       }
     }
@@ -150,9 +203,9 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
   // earlier use of this shared memory (the active list's neighbours, the delayed set) is complete
   __syncthreads();
   for (int k = 0; k < RD_D - 1; ++k) issue(k);
-  dfsum sr[NV], si[NV];
+  f2x2 H[NV], L[NV];  // (Re, Im) of the running sums: hi parts, lo parts
 #pragma unroll
-  for (int q = 0; q < NV; ++q) sr[q] = si[q] = dfsum{0.f, 0.f};
+  for (int q = 0; q < NV; ++q) H[q] = L[q] = 0ull;
   for (int k = 0; k < nst; ++k) {
     __syncwarp();  // this warp is done with slot (k - 1) % RD_D, which stage k + RD_D - 1 refills
     issue(k + RD_D - 1);
@@ -160,18 +213,21 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
     __syncwarp();                                                         // ... for every lane of the warp
     if (!live) continue;
     const unsigned char* st = area + (size_t)(k % RD_D) * stage;
-    const float4* gst = reinterpret_cast<const float4*>(st) + grp * R * gs + jl;
-    const float4* xst = reinterpret_cast<const float4*>(st + oX) + warp * NV * R;
+    const ulonglong2* gst = reinterpret_cast<const ulonglong2*>(st) + grp * R * gs + jl;
+    const ulonglong2* xst = reinterpret_cast<const ulonglong2*>(st + oX) + warp * NV * R * 2;
     for (int r = 0; r < R; ++r) {
       if (k * S + grp + ng * r >= m) break;
-      const float4 gg = gst[r * gs];
+      const ulonglong2 g = gst[r * gs];  // (Re hi, Im hi), (Re lo, Im lo) of G
+      float gr1, gi1, gr2, gi2;
+      upk2(g.x, gr1, gi1);
+      upk2(g.y, gr2, gi2);
+      const f2x2 na1 = pk2(-gr1, -gi1), na2 = pk2(-gr2, -gi2);
+      const f2x2 b1 = pk2(-gi1, gr1), nb1 = pk2(gi1, -gr1), nb2 = pk2(gi2, -gr2);
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const float4 x = xst[q * R + r];
-        df_madd(sr[q], gg.x, gg.y, x.x, x.y);    // Re G Re x
-        df_madd(sr[q], -gg.z, -gg.w, x.z, x.w);  // - Im G Im x
-        df_madd(si[q], gg.x, gg.y, x.z, x.w);    // Re G Im x
-        df_madd(si[q], gg.z, gg.w, x.x, x.y);    // Im G Re x
+        const ulonglong2 xr = xst[(q * R + r) * 2], xi = xst[(q * R + r) * 2 + 1];
+        df_madd2(H[q], L[q], g.x, na1, na2, xr.x, xr.y);  // (Re G Re x, Im G Re x)
+        df_madd2(H[q], L[q], b1, nb1, nb2, xi.x, xi.y);   // (-Im G Im x, Re G Im x)
       }
     }
   }
@@ -180,7 +236,12 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
   float4* part = reinterpret_cast<float4*>(area);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    if (live) part[tid] = make_float4(sr[q].hi, sr[q].lo, si[q].hi, si[q].lo);
+    if (live) {
+      float rh, ih, rl, il;
+      upk2(H[q], rh, ih);
+      upk2(L[q], rl, il);
+      part[tid] = make_float4(rh, rl, ih, il);
+    }
     __syncthreads();
     if (tid < own) {
       dfsum re{0.f, 0.f}, im{0.f, 0.f};

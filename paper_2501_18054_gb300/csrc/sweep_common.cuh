@@ -50,8 +50,8 @@ struct SweepArgs {
   void* rec;  // [2][P] candidate records
   unsigned long long* slots;  // [2][P] round words of the mixed search, 128 B apart
   int* actg;                  // n: active-pixel list of the last refresh (written by CTA 0)
-  const float4* G2;           // n x n: G as FP32 pairs (Re hi, Re lo, Im hi, Im lo)
-  float4* xs;                 // (1 + n_o) x n: x = v.[e, T] at the active pixels, as FP32 pairs
+  const float4* G2;           // n x n: G as FP32 pairs (Re hi, Im hi, Re lo, Im lo)
+  float4* xs;                 // (1 + n_o) x n x 2: x = v.[e, T] at the active pixels, FP32 pairs, each part twice
 };
 
 // a CTA's candidate of one scoring round, with the state the pivot needs
