@@ -66,6 +66,7 @@ Layout make_layout(const pngf_config& cfg) {
   // mixed path: G as FP32 pairs (double-float refresh residual) and the split refined vectors
   L.gsplit = take(mixed ? n * n * 4 * sizeof(float) : 0);
   L.xs = take(mixed ? (1 + n_o) * n * 8 * sizeof(float) : 0);
+  L.xadd = take(mixed ? (size_t)L.R * 4 * sizeof(float) : 0);  // alpha_i of the mixed search as double-words
   L.ipiv = take(2 * n * sizeof(int));
   L.snapW = take(L.snapW_bytes);
   L.snapState = take(L.state_bytes + sizeof(Control));

@@ -119,7 +119,7 @@ __device__ __forceinline__ void latch_status(Control* ctl, int s) {
 
 // ---------------------------------------------------------------- context
 struct Layout {
-  size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, slots, actg, gsum, gsplit, xs, cbuf, ipiv, rbuf,
+  size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, slots, actg, gsum, gsplit, xs, xadd, cbuf, ipiv, rbuf,
       snapW, snapState, ctl, total;
   size_t snapW_bytes;  // bytes of the maintained inverse copied by snapshot
   size_t tcimg, tcimgA_bytes, tcimg_bytes;  // mixed path: operand images of the tensor-core fold

@@ -52,6 +52,7 @@ struct SweepArgs {
   int* actg;                  // n: active-pixel list of the last refresh (written by CTA 0)
   const float4* G2;           // n x n: G as FP32 pairs (Re hi, Im hi, Re lo, Im lo)
   float4* xs;                 // (1 + n_o) x n x 2: x = v.[e, T] at the active pixels, FP32 pairs, each part twice
+  float4* xadd;               // R: alpha_i of the mixed search as double-word pairs, until copied to xa
 };
 
 // a CTA's candidate of one scoring round, with the state the pivot needs
@@ -923,6 +924,7 @@ SweepArgs make_args(pngf_ctx* c) {
   a.actg = at<int>(c, L.actg);
   a.G2 = a.mixed ? at<float4>(c, L.gsplit) : nullptr;
   a.xs = a.mixed ? at<float4>(c, L.xs) : nullptr;
+  a.xadd = a.mixed ? at<float4>(c, L.xadd) : nullptr;
   a.tensor_fold = c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold;
   a.tcimgA = reinterpret_cast<unsigned char*>(c->ws) + L.tcimg;
   a.tcimgB = a.tcimgA + L.tcimgA_bytes;

@@ -22,6 +22,7 @@
 
 #include "flush_tc.cuh"
 #include "refresh_df.cuh"
+#include "dd.cuh"
 
 namespace pngf {
 namespace {
@@ -80,14 +81,33 @@ static_assert(kOwnStateSmem % 1024 == 0, "fold operands stay 1024-B aligned");
 struct MixRecord {
   long long key;  // FIRST: visiting position
   double gain;    // BEST: gain of the candidate
-  double f_new;   // objective after the flip
+  dd f_new;       // objective after the flip
   int pixel;
   int b;
-  c128 alpha, coef;
-  c128 dv;
-  c128 Tk[kMaxPorts];  // scaled rows T'_p at the pixel
+  cdd alpha, coef;
+  cdd Tk[kMaxPorts];  // scaled rows T'_p at the pixel
 };
 static_assert(sizeof(MixRecord) <= kRecordBytes, "record slot");
+static_assert(offsetof(MixRecord, f_new) % 8 == 0 && offsetof(MixRecord, alpha) % 8 == 0 &&
+                  offsetof(MixRecord, coef) % 8 == 0 && offsetof(MixRecord, Tk) % 8 == 0,
+              "record words: every double-word on its own 8-byte word");
+
+// the pivot of a kept flip, as every CTA holds it
+struct MixPivot {
+  int k;
+  cdd alpha, coef;  // coef = alpha e_k
+  cdd Tk[kMaxPorts];
+};
+
+// FP64 <-> double-word conversions (FP64 instructions: used at set-up, after a
+// refresh and at the end, never on the per-flip chain)
+__device__ __forceinline__ dd dd_from(double x) {
+  const float hi = (float)x;
+  return dd{hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ cdd cdd_from(c128 x) { return cdd{dd_from(x.x), dd_from(x.y)}; }
+__device__ __forceinline__ double dd_to(dd x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ c128 cdd_to(cdd x) { return mk(dd_to(x.re), dd_to(x.im)); }
 
 __device__ __forceinline__ MixRecord* mrec_at(const SweepArgs& a, int par, int q) {
   return reinterpret_cast<MixRecord*>(a.rec) + (size_t)par * gridDim.x + q;
@@ -96,13 +116,20 @@ __device__ __forceinline__ MixRecord* mrec_at(const SweepArgs& a, int par, int q
 __device__ __forceinline__ int owner_of(int k, int n, int P) { return (int)(((long long)(k + 1) * P - 1) / n); }
 
 // acc + the objective term of one port from |S_p|^2 (w_p |S_p|^2, or
-// w_p (1 - |S_p|)^2); the objective kind is a template parameter so that the
-// other kind's FP64 instructions are not issued predicated-off per pixel
+// w_p (1 - |S_p|)^2), in double-words; the objective kind is a template
+// parameter so that the other kind's instructions are not issued per pixel
 template <int OBJ>
-__device__ __forceinline__ double obj_acc(double w, double a2, double acc) {
-  if (OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER) return fma(w, a2, acc);
-  const double m = 1.0 - sqrt(a2);
-  return fma(w, m * m, acc);
+__device__ __forceinline__ dd obj_acc(dd w, dd a2, dd acc) {
+  if (OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER) return dd_add(acc, dd_mul(w, a2));
+  const dd m = dd_sub(dd_of(1.0f), dd_sqrt(a2));
+  return dd_add(acc, dd_mul(w, dd_mul(m, m)));
+}
+// improvement bound f + thr (maximised) or f - thr (minimised), thr = tau max(|f|, 1e-30)
+template <int OBJ>
+__device__ __forceinline__ dd improve_bound(dd f, dd tau) {
+  const dd af = dd_abs(f);
+  const dd thr = dd_mul(af.hi > 1e-30f ? af : dd_of(1e-30f), tau);
+  return OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? dd_add(f, thr) : dd_sub(f, thr);
 }
 
 // waits (bounded) for CTA q's word of round `seq`; returns its key
@@ -129,23 +156,26 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   const int own = pe - pb;
   Control* ctl = a.ctl;
   // own-pixel state (thread jl < own scores pixel pb + jl)
-  c128* s_T = reinterpret_cast<c128*>(dyn_smem);  // [kMaxPorts][kOwnMax], T'_p,j = T_p,j scale_p
-  c128* s_diag = s_T + kMaxPorts * kOwnMax;
-  c128* s_e = s_diag + kOwnMax;
-  c128* s_dv = s_e + kOwnMax;
-  c128* s_idv = s_dv + kOwnMax;                                    // 1 / dv (0 where dv = 0)
-  double* s_dv2 = reinterpret_cast<double*>(s_idv + kOwnMax);      // |dv|^2
+  // (double-words, so that the per-flip chain runs on the FP32 pipe; dv itself stays FP64)
+  cdd* s_T = reinterpret_cast<cdd*>(dyn_smem);  // [kMaxPorts][kOwnMax], T'_p,j = T_p,j scale_p
+  cdd* s_diag = s_T + kMaxPorts * kOwnMax;
+  cdd* s_e = s_diag + kOwnMax;
+  c128* s_dv = reinterpret_cast<c128*>(s_e + kOwnMax);
+  cdd* s_idv = reinterpret_cast<cdd*>(s_dv + kOwnMax);             // 1 / dv (0 where dv = 0)
+  dd* s_dv2 = reinterpret_cast<dd*>(s_idv + kOwnMax);                // |dv|^2
   unsigned char* work = reinterpret_cast<unsigned char*>(dyn_smem) + kOwnStateSmem;
   __shared__ int s_pos[kOwnMax];
   __shared__ unsigned char s_b[kOwnMax];
   __shared__ float2 s_wk[kOwnMax];
-  __shared__ c128 s_c[kOwnMax], s_ac[kOwnMax];  // column entry c_j and alpha c_j of the kept flip
+  __shared__ float2 s_c[kOwnMax];  // column entry c_j of the kept flip (FP32)
+  __shared__ cdd s_ac[kOwnMax];     // alpha c_j
   __shared__ float2 s_beta[kMaxDelay], s_alpha[kMaxDelay];
-  __shared__ c128 s_S[kMaxPorts];      // scaled port amplitudes S_p = (o_p - off_p) scale_p
+  __shared__ cdd s_S[kMaxPorts];       // scaled port amplitudes S_p = (o_p - off_p) scale_p
+  __shared__ dd s_w[kMaxPorts], s_tau;  // objective weights w_p, acceptance tolerance tau
   __shared__ c128 s_o[kMaxPorts];      // port amplitudes after a refresh
   __shared__ c128 s_iscale[kMaxPorts];  // 1 / scale_p
-  __shared__ double s_f, s_thr, s_fthr;  // objective, acceptance margin, improvement bound
-  __shared__ Pivot s_pv;
+  __shared__ dd s_f, s_fthr;  // objective, improvement bound
+  __shared__ MixPivot s_pv;
   __shared__ ObjParams s_op;
   __shared__ int s_fail, s_bad;
   // delayed columns of the own pixels between folds, column-major: Xs[i * OS + jl] = x_i[pb + jl]
@@ -159,23 +189,26 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     s_op = a.op;
     FOR_PORTS(p, n_o) {
       s_iscale[p] = cdiv(mk(1.0, 0.0), a.op.scale[p]);
-      s_S[p] = cmul(csub(ctl->o[p], a.op.off[p]), a.op.scale[p]);
+      s_S[p] = cdd_from(cmul(csub(ctl->o[p], a.op.off[p]), a.op.scale[p]));
+      s_w[p] = dd_from(a.op.w[p]);
     }
-    s_f = ctl->f;
-    s_thr = accept_threshold(a.op, s_f);
-    s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? s_f + s_thr : s_f - s_thr;
+    s_tau = dd_from(a.op.tau);
+    s_f = dd_from(ctl->f);
+    const double thr = accept_threshold(a.op, ctl->f);
+    s_fthr = dd_from(OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? ctl->f + thr : ctl->f - thr);
     s_fail = 0;
   }
   for (int jl = tid; jl < own; jl += blockDim.x) {
     const int j = pb + jl;
     const c128 dv = a.dv[j];
-    s_diag[jl] = a.diag[j];
-    s_e[jl] = a.e[j];
+    s_diag[jl] = cdd_from(a.diag[j]);
+    s_e[jl] = cdd_from(a.e[j]);
     s_dv[jl] = dv;
-    s_dv2[jl] = cabs2(dv);
-    s_idv[jl] = cabs2(dv) > 0.0 ? cdiv(mk(1.0, 0.0), dv) : mk(0.0, 0.0);
+    s_dv2[jl] = dd_from(cabs2(dv));
+    s_idv[jl] = cdd_from(cabs2(dv) > 0.0 ? cdiv(mk(1.0, 0.0), dv) : mk(0.0, 0.0));
     s_b[jl] = a.b[j];
-    for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cmul(a.T[(size_t)p * a.ldt + j], a.op.scale[p]);
+    for (int p = 0; p < n_o; ++p)
+      s_T[p * kOwnMax + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], a.op.scale[p]));
     if (!a.order) s_pos[jl] = j;
   }
   for (int q = tid; q < own * r; q += blockDim.x) {
@@ -190,16 +223,16 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   auto store_et = [&](bool with_diag) {
     for (int jl = tid; jl < own; jl += blockDim.x) {
       const int j = pb + jl;
-      a.e[j] = s_e[jl];
-      if (with_diag) a.diag[j] = s_diag[jl];
-      for (int p = 0; p < n_o; ++p) a.T[(size_t)p * a.ldt + j] = cmul(s_T[p * kOwnMax + jl], s_iscale[p]);
+      a.e[j] = cdd_to(s_e[jl]);
+      if (with_diag) a.diag[j] = cdd_to(s_diag[jl]);
+      for (int p = 0; p < n_o; ++p) a.T[(size_t)p * a.ldt + j] = cmul(cdd_to(s_T[p * kOwnMax + jl]), s_iscale[p]);
     }
   };
   auto load_et = [&]() {
     for (int jl = tid; jl < own; jl += blockDim.x) {
       const int j = pb + jl;
-      s_e[jl] = a.e[j];
-      for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cmul(a.T[(size_t)p * a.ldt + j], s_op.scale[p]);
+      s_e[jl] = cdd_from(a.e[j]);
+      for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], s_op.scale[p]));
     }
   };
   auto load_pos = [&]() {
@@ -243,7 +276,15 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   if (a.tensor_fold) tc_setup(tcs, s_tc_bars, &s_tmem, tc_tmem_cols(2));
   // the fold reuses the shared memory of the delayed rows: they are in global
   // X as well and the delayed set is empty afterwards
+  // alpha_i kept since the last fold (or this call's start) as double-words -> FP64 xa
+  int r_dd = r;  // first entry of xadd written by this call
+  auto alpha_to_fp64 = [&]() {
+    if (cta == 0)
+      for (int i = r_dd + tid; i < r; i += blockDim.x) a.xa[i] = cdd_to(reinterpret_cast<const cdd*>(a.xadd)[i]);
+    r_dd = 0;
+  };
   auto flush = [&]() -> bool {
+    alpha_to_fp64();  // before the barrier that publishes it to every CTA's fold
     if (!grid_sync(ctl)) return false;
     if (a.tensor_fold) {
       tc_prepare(a, r, a.tcimgA, a.tcimgB, (long long)blockIdx.x * blockDim.x + threadIdx.x,
@@ -269,29 +310,28 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   const long long max_steps = a.n_sweeps;
   while (!failed && status != PNGF_EINVAL) {
     // improving: f_new > f + thr (maximised) or f_new < f - thr (minimised); the
-    // bounds are formed once per kept flip by the thread that sets f, so that
-    // the warps that do not score issue no FP64 instruction here
-    const double f = s_f, thr = s_thr, fthr = s_fthr;
+    // bound is formed once per kept flip by the thread that sets f
+    const dd fthr = s_fthr;
     const int par = (int)(round & 1);
     const unsigned seq = (unsigned)((round + 1) & kSeqMask);
     unsigned long long* words = a.slots + (size_t)par * P * kSlotStride;
     // ---- score own pixels; the CTA's best candidate goes to its record, its key to its word
     long long key = kNoCand;
     {
-      double fn = 0.0;
-      c128 al = mk(0.0, 0.0), co = al;
+      dd fn = dd_of(0.0f);
+      cdd al = cdd_of(0.0f, 0.0f), co = al;
       bool ok = false;
-      if (tid < own) {
-        const c128 idv = s_idv[tid], w = s_diag[tid];
-        const c128 z = s_b[tid] ? mk(-idv.x - w.x, -idv.y - w.y) : mk(idv.x - w.x, idv.y - w.y);
-        const double z2 = cabs2(z);
-        if (!(z2 * s_dv2[tid] < 1e-28)) {  // |d_j| = |delta_j| |z_j|; singular candidates are skipped
-          const double iz = 1.0 / z2;
-          al = mk(z.x * iz, -z.y * iz);
-          co = cmul(al, s_e[tid]);
+      if (tid < own) {  // in double-words on the FP32 pipe
+        const cdd idv = s_idv[tid], w = s_diag[tid];
+        const cdd z = s_b[tid] ? cdd_sub(cdd{dd_neg(idv.re), dd_neg(idv.im)}, w) : cdd_sub(idv, w);
+        const dd z2 = cdd_abs2(z);
+        if (!(z2.hi * s_dv2[tid].hi < 1e-28f)) {  // |d_j| = |delta_j| |z_j|; singular candidates are skipped
+          const dd iz = dd_rcp(z2);
+          al = cdd{dd_mul(z.re, iz), dd_neg(dd_mul(z.im, iz))};
+          co = cdd_mul(al, s_e[tid]);
 #pragma unroll 1
           for (int p = 0; p < n_o; ++p)
-            fn = obj_acc<OBJ>(s_op.w[p], cabs2(cfma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
+            fn = obj_acc<OBJ>(s_w[p], cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
           ok = true;
         }
       }
@@ -304,14 +344,13 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         rc->b = s_b[tid];
         rc->alpha = al;
         rc->coef = co;
-        rc->dv = s_dv[tid];
         for (int p = 0; p < n_o; ++p) rc->Tk[p] = s_T[p * kOwnMax + tid];
       };
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
         long long cand = kNoCand;
         if (ok) {
           const int pos = s_pos[tid];
-          const bool improving = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fn > fthr : fn < fthr;
+          const bool improving = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? dd_gt(fn, fthr) : dd_lt(fn, fthr);
           if (pos >= t && improving) cand = ((long long)pos << kPixBits) | (pb + tid);
         }
         key = block_min_ll(cand);
@@ -320,7 +359,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         double g = -INFINITY;
         int pix = INT_MAX;
         if (ok) {
-          g = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fn - f : f - fn;
+          const dd f = s_f;
+          g = dd_to(OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? dd_sub(fn, f) : dd_sub(f, fn));
           pix = pb + tid;
         }
         double gb = g;
@@ -367,7 +407,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           g = mrec_at(a, par, tid)->gain;
         }
         block_best(g, pix);
-        if (pix != INT_MAX && g - thr > 0.0) k = pix;
+        // the best candidate is kept when it clears the improvement bound
+        if (pix != INT_MAX) {
+          const dd fb = mrec_at(a, par, owner_of(pix, n, P))->f_new;
+          if (OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? dd_gt(fb, fthr) : dd_lt(fb, fthr)) k = pix;
+        }
       }
     }
     ++round;
@@ -403,19 +447,23 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     //      load per lane (lane l: word l) and share the FP64 bookkeeping:
     //      0: pivot and f, 5: S(new), 6: FP32 copy of alpha, 7: trace (CTA 0).
     if (warp == 0 || (warp >= 5 && warp <= 7)) {
-      const double* rw = reinterpret_cast<const double*>(mrec_at(a, par, owner_of(k, n, P)));
-      constexpr int kWords = (int)(sizeof(MixRecord) / sizeof(double));
+      const unsigned long long* rw =
+          reinterpret_cast<const unsigned long long*>(mrec_at(a, par, owner_of(k, n, P)));
+      constexpr int kWords = (int)(sizeof(MixRecord) / 8);
       static_assert(kWords <= 32, "one record word per lane");
-      const double wv = lane < kWords ? rw[lane] : 0.0;
-      auto word = [&](int i) { return __shfl_sync(0xffffffffu, wv, i); };
+      const unsigned long long wv = lane < kWords ? rw[lane] : 0ull;
+      auto word = [&](int i) {  // word i of the record as a double-word
+        const unsigned long long u = __shfl_sync(0xffffffffu, wv, i);
+        return dd{__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32))};
+      };
       constexpr int oF = offsetof(MixRecord, f_new) / 8, oA = offsetof(MixRecord, alpha) / 8;
       constexpr int oC = offsetof(MixRecord, coef) / 8, oT = offsetof(MixRecord, Tk) / 8;
-      const c128 al = mk(word(oA), word(oA + 1)), co = mk(word(oC), word(oC + 1));
-      const double fnew = word(oF);
-      c128 tk = mk(0.0, 0.0);  // lane p < n_o: row p of T' at pixel k
+      const cdd al = cdd{word(oA), word(oA + 1)}, co = cdd{word(oC), word(oC + 1)};
+      const dd fnew = word(oF);
+      cdd tk = cdd_of(0.0f, 0.0f);  // lane p < n_o: row p of T' at pixel k
 #pragma unroll
       for (int p = 0; p < kMaxPorts; ++p) {
-        const c128 v = mk(word(oT + 2 * p), word(oT + 2 * p + 1));
+        const cdd v = cdd{word(oT + 2 * p), word(oT + 2 * p + 1)};
         if (lane == p) tk = v;
       }
       if (warp == 0) {
@@ -425,16 +473,17 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           s_pv.alpha = al;
           s_pv.coef = co;
           s_f = fnew;
-          s_thr = accept_threshold(s_op, fnew);
-          s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? fnew + s_thr : fnew - s_thr;
-          s_bad = !isfinite(fnew);
+          s_fthr = improve_bound<OBJ>(fnew, s_tau);
+          s_bad = !isfinite(fnew.hi);
         }
       } else if (warp == 5) {
-        // S(new) exactly as the scorer formed it for its objective
-        if (lane < n_o) s_S[lane] = cfma(co, tk, s_S[lane]);
+        // S(new) exactly as the scorer formed it
+        if (lane < n_o) s_S[lane] = cdd_fma(co, tk, s_S[lane]);
       } else if (warp == 6) {
-        if (lane == 0) s_alpha[r] = make_float2((float)al.x, (float)al.y);
+        if (lane == 0) s_alpha[r] = make_float2(al.re.hi, al.im.hi);  // alpha rounded to FP32
       } else if (cta == 0 && lane == 0) {
+        // warp 7: the trace and alpha as double-words, converted to FP64 off the
+        // chain (alpha before the next fold, the objectives at the end)
         if (n_acc < a.trace_cap) {
           if (a.trace) {
             int32_t* tr = a.trace + 4 * n_acc;
@@ -443,9 +492,9 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
             tr[2] = k;
             tr[3] = 0;
           }
-          if (a.trace_f) a.trace_f[n_acc] = fnew;
+          if (a.trace_f) *reinterpret_cast<dd*>(a.trace_f + n_acc) = fnew;
         }
-        a.xa[r] = al;
+        reinterpret_cast<cdd*>(a.xadd)[r] = al;
       }
     } else if (tid >= 32 && tid < 32 + r) {
       const int i = tid - 32;
@@ -508,9 +557,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           dy += s_part[q * kOwnMax + jl].y;
         }
         const float2 cf = make_float2(sx + dx, sy + dy);
-        const c128 cj = mk((double)cf.x, (double)cf.y);
-        s_c[jl] = cj;
-        s_ac[jl] = cmul(s_pv.alpha, cj);
+        s_c[jl] = cf;
+        s_ac[jl] = cdd_mul_cf(s_pv.alpha, cf.x, cf.y);
         const int j = pb + jl;
         Xs[r * OS + jl] = cf;
         a.X[(size_t)j * R + r] = cf;
@@ -531,12 +579,12 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       for (int q = warp & 3; q < nq; q += 4)
         for (int jl = (warp >> 2) * 32 + lane; jl < own; jl += kThreads / 4) {
           if (q == 0) {
-            s_diag[jl] = cfma(s_ac[jl], s_c[jl], s_diag[jl]);
+            s_diag[jl] = cdd_add(s_diag[jl], cdd_mul_cf(s_ac[jl], s_c[jl].x, s_c[jl].y));
           } else if (q == 1) {
-            s_e[jl] = cfma(s_pv.coef, s_c[jl], s_e[jl]);
+            s_e[jl] = cdd_add(s_e[jl], cdd_mul_cf(s_pv.coef, s_c[jl].x, s_c[jl].y));
           } else {
-            c128* tq = s_T + (q - 2) * kOwnMax + jl;
-            *tq = cfma(s_ac[jl], s_pv.Tk[q - 2], *tq);
+            cdd* tq = s_T + (q - 2) * kOwnMax + jl;
+            *tq = cdd_fma(s_ac[jl], s_pv.Tk[q - 2], *tq);
           }
         }
     }
@@ -576,11 +624,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         tick(11);
         load_et();
         ports_total(a, s_o);
-        if (tid < n_o) s_S[tid] = cmul(csub(s_o[tid], s_op.off[tid]), s_op.scale[tid]);
+        if (tid < n_o) s_S[tid] = cdd_from(cmul(csub(s_o[tid], s_op.off[tid]), s_op.scale[tid]));
         if (tid == 32) {
-          s_f = objective_of(s_op, s_o);
-          s_thr = accept_threshold(s_op, s_f);
-          s_fthr = OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? s_f + s_thr : s_f - s_thr;
+          const double f = objective_of(s_op, s_o), thr = accept_threshold(s_op, f);
+          s_f = dd_from(f);
+          s_fthr = dd_from(OBJ == PNGF_OBJ_MAX_WEIGHTED_POWER ? f + thr : f - thr);
         }
         __syncthreads();
         tick(5);
@@ -602,11 +650,15 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   }
   __syncthreads();
   store_et(true);
+  alpha_to_fp64();
+  if (cta == 0 && a.trace_f)  // the objectives of the trace, kept as double-words
+    for (long long i = tid; i < n_acc && i < a.trace_cap; i += blockDim.x)
+      a.trace_f[i] = dd_to(*reinterpret_cast<const dd*>(a.trace_f + i));
   if (a.tensor_fold) tc_teardown(tcs, failed);  // after a failure: bounded wait for what was issued
   if (cta == 0 && threadIdx.x == 0) {
     if (failed) status = PNGF_ETIMEOUT;
-    FOR_PORTS(p, n_o) ctl->o[p] = cadd(cmul(s_S[p], s_iscale[p]), s_op.off[p]);
-    ctl->f = s_f;
+    FOR_PORTS(p, n_o) ctl->o[p] = cadd(cmul(cdd_to(s_S[p]), s_iscale[p]), s_op.off[p]);
+    ctl->f = dd_to(s_f);
     ctl->since_refresh = since_refresh;
     ctl->r_delay = r;
     ctl->n_acc_total += (int)n_acc;
