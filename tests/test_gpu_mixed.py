@@ -153,6 +153,33 @@ def test_mixed_dbs_matches_oracle(P, fdfd64, name, delay_r, refresh_k, tensor_fo
     assert c[5] == len(ref_k) // delay_r  # flushes
 
 
+@pytest.mark.parametrize("mode", ["first", "best"])
+def test_mixed_min_objective_matches_oracle(P, fdfd64, mode):
+    """The minimised objective, f = sum_p w_p (1 - |S_p|)^2 (the insertion-loss
+    form, w = (0, 1)), through the mixed path with folds and refreshes: the
+    accepted sequence equals the oracle's (decision margins above 1e-5 |f| for
+    this start) and the final S-parameters agree within 1e-4."""
+    import dataclasses
+    case = dataclasses.replace(fdfd64, obj_kind=W.OBJ_MIN_INSERTION_LOSS, obj_weights=np.array([0.0, 1.0]))
+    p = O.Problem.from_case(case)
+    b0 = W.random_design(case.n_d, 4)
+    first = mode == "first"
+    n_sweeps = 3 if first else 40
+    order = np.tile(np.arange(case.n_d, dtype=np.int32), (n_sweeps, 1))
+    ref = O.dbs(p, b0, order, tau=1e-9, mode=O.FIRST_IMPROVEMENT if first else O.BEST_IMPROVEMENT)
+    assert ref.min_abs_margin > 1e-6 * abs(ref.f)
+    ctx = _ctx(P, case, mode=P.PNGF_FIRST_IMPROVEMENT if first else P.PNGF_BEST_IMPROVEMENT, tau=1e-9,
+               delay_r=16, refresh_k=32, tensor_fold=1)
+    ctx.factor(b0)
+    res = ctx.dbs_sweep(n_sweeps)
+    assert [int(r[2]) for r in res["trace"]] == [k for _, _, k, _ in ref.accepted]
+    assert np.array_equal(ctx.design(), ref.b)
+    f_trace = np.array([fa for _, _, _, fa in ref.accepted])
+    assert np.max(np.abs(res["trace_f"] - f_trace) / np.abs(f_trace)) < 1e-5
+    o, _ = ctx.eval_ports()
+    assert s_rel(case, o, ref.o) < 1e-4
+
+
 def test_mixed_restore_replays(P, fdfd64):
     ctx = _ctx(P, fdfd64, delay_r=8, refresh_k=16)
     ctx.factor(W.random_design(fdfd64.n_d, 0))
