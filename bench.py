@@ -72,7 +72,10 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--runs", type=int, default=4,
                     help="independent runs per GPU (random starts), launched side by side on their own streams")
-    ap.add_argument("--refresh-k", type=int, default=64)
+    # kept flips between refreshes of the mixed path (a multiple of --delay-r): 256 keeps the
+    # S-parameters within ~2e-6 of the oracle at this workload (the metric's bar is 1e-4), and
+    # every line reports the measured error and whether the final designs equal the FP64 path's
+    ap.add_argument("--refresh-k", type=int, default=256)
     ap.add_argument("--tau", type=float, default=1e-9)
     ap.add_argument("--cpu-sample-evals", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
