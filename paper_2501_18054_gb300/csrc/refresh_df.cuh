@@ -23,19 +23,9 @@ namespace {
 // removes.  Round-to-nearest intrinsics throughout keep the compiler from
 // contracting a product and a sum into one FMA, which would break the exact
 // transformations.
-struct dfsum {
+struct dfsum {  // a running sum hi + lo (the partial sums of the groups)
   float hi, lo;
 };
-__device__ __forceinline__ void df_madd(dfsum& s, float a1, float a2, float b1, float b2) {
-  const float p = __fmul_rn(a1, b1);
-  const float err = __fmaf_rn(a1, b1, -p);
-  const float cross = __fmaf_rn(a1, b2, __fmaf_rn(a2, b1, err));
-  const float t = __fadd_rn(s.hi, p);
-  const float bv = __fsub_rn(t, s.hi);
-  const float rnd = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-  s.hi = t;
-  s.lo = __fadd_rn(s.lo, __fadd_rn(rnd, cross));
-}
 __device__ __forceinline__ double df_value(dfsum s) { return (double)s.hi + (double)s.lo; }
 // ---- packed pairs: two FP32 lanes in one 64-bit operand of the f32x2 instructions
 typedef unsigned long long f2x2;
@@ -66,9 +56,11 @@ __device__ __forceinline__ f2x2 fma2(f2x2 a, f2x2 b, f2x2 c) {
   return r;
 }
 // Two double-float multiply-adds in one instruction stream, one per lane of the
-// pairs: (H, L) += (a1 + a2)(b1 + b2) with na1 = -a1 and na2 = -a2 given, so that
-// the exact error of the product comes out negated, -err = fma(-a1, b1, p), and
-// no negation is needed: the same steps as df_madd, with -cross subtracted.
+// pairs: (H, L) += (a1 + a2)(b1 + b2), with na1 = -a1 and na2 = -a2 given.
+//   p = fl(a1 b1); -err = fma(-a1, b1, p) (exact); -cross = -(a1 b2 + a2 b1 + err);
+//   TwoSum(H, p) = t + rnd exactly; H = t; L += rnd + cross.
+// The negated operands give the error terms with the opposite sign, so no
+// negation instruction is needed.
 __device__ __forceinline__ void df_madd2(f2x2& H, f2x2& L, f2x2 a1, f2x2 na1, f2x2 na2, f2x2 b1, f2x2 b2) {
   const f2x2 p = mul2(a1, b1);
   const f2x2 nerr = fma2(na1, b1, p);
