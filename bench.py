@@ -36,14 +36,40 @@ WORKLOAD = "fdfd256_nd4096"  # 256^2 FDFD, 16-cell PML, eps=2.2 slab, 64x64 desi
 # DRAM traffic of the search kernel from one ncu capture (profiles/dbs_mixed_kernel_fdfd256_nd4096.md:
 # one launch = one full run, seed 0): measured read + write bytes over the algorithmic bytes of
 # that launch.  A step's traffic is this ratio times the step's algorithmic bytes, reported only
-# while the kernel sources are the captured ones (fingerprint below), else null.
+# while the kernel code is the captured one (fingerprint of the sources without comments), else null.
 TRAFFIC_CAPTURE = {"kernel": "dbs_mixed_kernel", "workload": "fdfd256_nd4096",
                    "measured_bytes": 2.856513e9 + 1.077680e9, "algorithmic_bytes": 4509239696.0,
-                   "sources_sha256": "3fa7ad552b6a03df2cf9c2accf7b2c5a4bf4ce38d38721475c9f6d5d29115b76"}
+                   "sources_sha256": "ead417b90caab5d582e95a3fd064e23aa30c1f564c57002369240074a13c1072"}
+
+
+def _code_only(src: str) -> str:
+    """C/C++ source without its comments and blank space, so that an edit of the
+    comments alone leaves the fingerprint of the code unchanged; string and
+    character literals are kept as they are."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            i = src.find("\n", i)
+            i = n if i < 0 else i
+        elif src.startswith("/*", i):
+            i = src.find("*/", i + 2)
+            i = n if i < 0 else i + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
 
 
 def sources_fingerprint() -> str:
-    """sha256 over the kernel sources (csrc/*.cu, *.cuh) and the C ABI header."""
+    """sha256 over the code (comments and blank space removed) of the kernel
+    sources (csrc/*.cu, *.cuh) and the C ABI header."""
     import glob
     import hashlib
     files = sorted(glob.glob(os.path.join(ROOT, "paper_2501_18054_gb300", "csrc", "*.cu")) +
@@ -52,8 +78,8 @@ def sources_fingerprint() -> str:
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -1,19 +1,19 @@
 // Direct binary search on the device, mixed-precision path.
 //
 // The maintained inverse W = M^-1 G (the paper's C~^-1, Supplementary Note 4)
-// is kept as a planar FP32 copy W_lo plus a delayed FP64 rank-r correction:
+// is kept as a planar FP32 copy W_lo plus a delayed rank-r correction:
 //   W = W_lo + sum_{i<r} alpha_i x_i x_i^T,   x_i = column of W at kept flip i.
-// Everything that decides a flip stays FP64: diag(W), e, T, o, the
-// Sherman-Morrison denominators d_k and alpha (Eqs. 9 and 14).  Per kept flip
-// of pixel k only the column c = W[:,k] is needed:
+// Per kept flip of pixel k only the column c = W[:,k] is needed:
 //   c_j = W_lo(k, j) + sum_{i<r} (alpha_i x_i[k]) x_i[j]      (FP32 arithmetic)
-// which updates diag(W), e and T in FP64 and is appended to the delayed set.
-// On GB300 the FP64 pipe retires 2 DFMA per clock per SM (1/64 of FP32), so
-// everything that only has to be FP32-accurate runs on the FP32 pipe.
-// Every R kept flips the delayed set is folded into W_lo with one rank-R
-// product over the upper triangle (the paper's O(N_opt^2) update of
-// Supplementary Note 3, done once per R flips), and every refresh_k flips e
-// and T are refined in FP64 against G.
+// which updates diag(W), e and T and is appended to the delayed set.  What
+// decides a flip, diag(W), e, T, o, the Sherman-Morrison denominators d_k and
+// alpha (Eqs. 9 and 14), is carried as double-words (FP32 pairs, ~48 bits,
+// dd.cuh), so the whole per-flip chain runs on the FP32 pipe: on GB300 the
+// FP64 pipe retires one warp instruction per 64 cycles on each SM
+// sub-partition.  Every R kept flips the delayed set is folded into W_lo with
+// one rank-R product over the upper triangle on the tensor cores (the paper's
+// O(N_opt^2) update of Supplementary Note 3, done once per R flips), and every
+// refresh_k flips e and T are refined against G with a double-float residual.
 //
 // Each CTA publishes its best candidate together with the pixel state the
 // pivot needs, and the CTAs agree on the kept flip by exchanging one word
@@ -41,16 +41,15 @@ namespace {
 // delayed rows X[own]) lives in shared memory between refreshes; only b and v
 // of the flipped pixel and the appended column of X are written through.
 //
-// FP64 on GB300 retires one warp instruction per 64 cycles on each SM
-// sub-partition whatever the number of active lanes, so the per-flip FP64
-// chain is kept short: the score needs one real division,
+// The per-flip chain is kept short: the score needs one reciprocal,
 //   alpha_j = 1 / z_j,  z_j = 1/delta_j - W_jj   (= delta_j / d_j, Eq. 14),
 // with 1/delta_j = -+1/dv_j tabulated, the rows of T are kept pre-multiplied by
 // the port scales so that S_p(new) = S_p + coef T'_p,j is one complex FMA,
 // the winner's record carries f(new) (every CTA forms S(new) with the same
-// operations the scorer used, off the critical path), and the FP64 state
-// update spreads diag, e and the rows of T over warps of different
-// sub-partitions.
+// operations the scorer used, off the critical path), and the state update
+// spreads diag, e and the rows of T over warps of different sub-partitions.
+// FP64 appears only at set-up, after a refresh, before a fold (alpha for the
+// fold's operands) and at the end (state, trace objectives).
 constexpr int kOwnMax = 128;                                       // pixels per CTA
 constexpr int kSlotStride = 16;                                    // 64-bit words between two CTAs' words
 constexpr int kSeqShift = 44;
