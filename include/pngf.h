@@ -70,6 +70,10 @@ typedef enum {
   PNGF_ECAPACITY = 8      /* trace buffer full (the sweep stopped early) */
 } pngf_status;
 
+/* PNGF_FP64: every step in FP64.  PNGF_MIXED: an FP32 maintained inverse with a
+ * delayed rank-delay_r correction, the decision state (diag W, e, T, o, f) as
+ * FP32 pairs (~48 bits, FP32 exponent range: magnitudes and their squares must
+ * stay within about 1e+-38), refreshed against G every refresh_k flips. */
 typedef enum { PNGF_FP64 = 0, PNGF_MIXED = 1 } pngf_precision;
 typedef enum { PNGF_FIRST_IMPROVEMENT = 0, PNGF_BEST_IMPROVEMENT = 1 } pngf_dbs_mode;
 typedef enum {
@@ -85,8 +89,9 @@ typedef struct {
   int32_t precision;  /* pngf_precision */
   int32_t mode;       /* pngf_dbs_mode */
   int32_t objective;  /* pngf_objective */
-  int32_t refresh_k;  /* FP64 iterative-refinement refresh of e, T, o every refresh_k
-                         accepted flips (0 = never) */
+  int32_t refresh_k;  /* iterative-refinement refresh of e, T, o every refresh_k accepted
+                         flips (0 = never): residual against G in FP64 (PNGF_FP64) or in
+                         FP32-pair arithmetic (PNGF_MIXED, a multiple of delay_r) */
   int32_t delay_r;    /* PNGF_MIXED: flips accumulated before the maintained inverse is
                          updated in one rank-delay_r product (1..128); ignored for FP64 */
   int32_t n_ctas;     /* persistent sweep grid (0 = one per SM, capped by occupancy) */
@@ -241,7 +246,7 @@ pngf_status pngf_restore(pngf_ctx* ctx);
  * phase, host int64 x 16: [0] scoring, [1] wait after scoring, [2] selection,
  * pivot and column gather, [3] wait before the update (FP64) / flush of the
  * delayed set (mixed), [4] state update (and the rank-1 update of W on the
- * FP64 path), [5] FP64 refreshes, [6] sweep set-up, [7] whole kernel,
+ * FP64 path), [5] refreshes, [6] sweep set-up, [7] whole kernel,
  * [8..11] refresh sub-phases (x, residual, correction, ports), [12..15] 0.
  * Synchronizes the stream.
  */
