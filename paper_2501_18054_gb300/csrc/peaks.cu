@@ -1,5 +1,5 @@
-// Throughput probes for the roofline denominators that the driver does not
-// measure: FP64 and FP32 fused multiply-add rates of the SIMT pipes.  Each
+// Throughput probes for the roofline denominators that the measured-peaks file
+// does not hold: FP64 and FP32 fused multiply-add rates of the SIMT pipes.  Each
 // thread runs eight independent FMA chains so that latency is hidden; the
 // result is 2 * FMAs / elapsed time (CUDA events on the given stream).
 #include <cuda_runtime.h>
