@@ -33,6 +33,7 @@ import dataclasses
 import hashlib
 import json
 import os
+import tempfile
 from typing import Optional, Sequence
 
 import numpy as np
@@ -41,6 +42,7 @@ OBJ_MAX_WEIGHTED_POWER = 0  # f = sum_p w_p |S_p|^2, maximised
 OBJ_MIN_INSERTION_LOSS = 1  # f = sum_p w_p (1 - |S_p|)^2, minimised
 
 LAMBDA_CELLS = 20.0  # dx = lambda / 20 in every workload
+RECIPE_VERSION = "2"  # part of every cache key: bump when a generated array changes
 K_CELL = 2.0 * np.pi / LAMBDA_CELLS  # k0 * dx
 
 
@@ -257,7 +259,7 @@ def make_fdfd_case(name, cache: bool = True) -> Case:
     """Build an FDFD workload by name (see ``SPECS``) or from an ``FdfdSpec``."""
     spec = SPECS[name] if isinstance(name, str) else name
     name = spec.name
-    key = hashlib.sha1(json.dumps(dataclasses.asdict(spec), default=str).encode()).hexdigest()[:12]
+    key = hashlib.sha1((json.dumps(dataclasses.asdict(spec), default=str) + RECIPE_VERSION).encode()).hexdigest()[:12]
     path = _cache_path(f"{name}_{key}.npz") if cache else None
     if path and os.path.exists(path):
         return _load_case(path)
@@ -304,7 +306,10 @@ def _build_fdfd(spec: FdfdSpec) -> Case:
     G_od = -np.ascontiguousarray(adj[dnodes, :].T)
     dv = np.full(n_d, k * k * (spec.eps_on - spec.eps_off), dtype=np.complex128)
     if spec.norm == "incident":
-        s_off = c_o.copy()
+        # the empty-design field at every port: the source-side port reports the
+        # scattered part (S11 = (o_1 - c_o,1)/c_o,1), every other port the total
+        # transmitted field (T_p1 = o_p/c_o,p)
+        s_off = np.array([c_o[0]] + [0.0] * (len(c_o) - 1), dtype=np.complex128)
         s_scale = 1.0 / c_o
     else:
         # reference: the same source in the unbroken waveguide gives the incident mode amplitude
@@ -348,7 +353,7 @@ def make_hankel_case(side: int = 128, n_ports: int = 4, ring_radius_lambda: floa
     from scipy.special import hankel1
 
     name = name or f"hankel{side}"
-    key = f"{name}_{side}_{n_ports}_{ring_radius_lambda}_{eps_off}_{eps_on}"
+    key = f"{name}_{side}_{n_ports}_{ring_radius_lambda}_{eps_off}_{eps_on}_{RECIPE_VERSION}"
     path = _cache_path(hashlib.sha1(key.encode()).hexdigest()[:12] + f"_{name}.npz") if cache else None
     if path and os.path.exists(path):
         return _load_case(path)
@@ -428,7 +433,9 @@ def get_case(name: str) -> Case:
 
 
 def _cache_path(fname: str) -> Optional[str]:
-    d = os.environ.get("PNGF_CACHE_DIR", "/tmp/pngf_cache")
+    """Cache file for generated inputs: $PNGF_CACHE_DIR, else pngf_cache in the
+    system's temporary directory; PNGF_CACHE_DIR=off disables the cache."""
+    d = os.environ.get("PNGF_CACHE_DIR") or os.path.join(tempfile.gettempdir(), "pngf_cache")
     if d in ("", "0", "off"):
         return None
     os.makedirs(d, exist_ok=True)

@@ -199,3 +199,59 @@ def test_planted_mistakes_are_caught(fdfd64, monkeypatch):
     monkeypatch.setattr(O.pngf_oracle, "port_amplitudes", lambda God, co, v, e: co + God @ e)
     ev = O.evaluate(p, b)
     assert np.max(np.abs(ev.o - o_full)) > 1e-6 * np.max(np.abs(o_full)), "dropped V in ports"
+
+
+def _full_structure_S(case, b):
+    """S-parameters of design b from direct sparse solves of full structures only.
+
+    The definition is applied to full-solve port amplitudes, independently of
+    the reduced system and of the oracle's affine map:
+      free-space line ports ("incident"): S11 = (o_1 - o_1^empty)/o_1^empty and
+        T21 = o_2/o_2^empty, the empty design's fields as the incident wave;
+      waveguide ports ("reference"): S11 = (o_1 - a_1)/a_1 and S21 = o_2/a_2,
+        a = the same source's mode amplitudes in the unbroken guide.
+    """
+    spec = W.SPECS[case.name]
+    _, o = _full_structure(case, b)
+    if spec.norm == "incident":
+        _, a = _full_structure(case, np.zeros(case.n_d, np.uint8))
+    else:
+        _, a = W.solve_full(spec, W._eps_grid(spec, with_slab_through_design=True))
+    return np.array([(o[0] - a[0]) / a[0]] + [o[p] / a[p] for p in range(1, len(o))])
+
+
+@pytest.mark.parametrize("name,seed", [("fdfd64", 3), ("fdfd64", 8), ("fdfd128_metal", 5)])
+def test_s_params_equal_full_structure(name, seed, fdfd64, metal128):
+    """The oracle's S (evaluate, then the affine map) equals S from full solves."""
+    case = fdfd64 if name == "fdfd64" else metal128
+    b = W.random_design(case.n_d, seed)
+    S = O.evaluate(O.Problem.from_case(case), b).S
+    S_full = _full_structure_S(case, b)
+    assert np.max(np.abs(S - S_full)) <= 1e-10 * max(1.0, np.max(np.abs(S_full)))
+    # the configured objective of the free-space case is |T21|^2 = |o_2/o_2^empty|^2
+    if name == "fdfd64":
+        assert O.Problem.from_case(case).obj_weights.tolist() == [0.0, 1.0]
+        f = O.evaluate(O.Problem.from_case(case), b).f
+        assert abs(f - abs(S_full[1]) ** 2) <= 1e-10 * abs(f)
+
+
+def test_planted_s_param_mistakes_are_caught(fdfd64, metal128, monkeypatch):
+    """A plausible slip in the S map fails the full-structure S pin on some case."""
+    cases = [(fdfd64, 3), (metal128, 5)]
+    full = [_full_structure_S(c, W.random_design(c.n_d, s)) for c, s in cases]
+    plants = {
+        "offset after the scale": lambda o, off, sc: o * sc - off,
+        "divided by the scale": lambda o, off, sc: (o - off) / sc,
+        "offset added": lambda o, off, sc: (o + off) * sc,
+        "offset on the other port": lambda o, off, sc: (o - off[::-1]) * sc,
+        "scale of the other port": lambda o, off, sc: (o - off) * sc[::-1],
+        "conjugated scale": lambda o, off, sc: (o - off) * np.conj(sc),
+    }
+    for what, bad in plants.items():
+        monkeypatch.setattr(O.pngf_oracle, "s_params", bad)
+        worst = 0.0
+        for (c, s), Sf in zip(cases, full):
+            S = O.evaluate(O.Problem.from_case(c), W.random_design(c.n_d, s)).S
+            worst = max(worst, np.max(np.abs(S - Sf)) / np.max(np.abs(Sf)))
+        assert worst > 1e-6, what
+    monkeypatch.undo()

@@ -118,6 +118,14 @@ def test_lossless_two_port_conserves_energy(seed):
     assert abs(B2) < 1e-4 * abs(A1)  # nothing comes back from the right PML
     assert abs(abs(S11) ** 2 + abs(S21) ** 2 - 1.0) < 1e-4
     assert abs(S11) > 1e-3  # the design actually scatters
+    # the oracle's S-parameters (the recipe's affine map of the reduced-system
+    # ports) are these modal values: port 1's line reports the reflected wave,
+    # port 2's line the transmitted one relative to the empty guide's
+    S = O.evaluate(p, b).S
+    F2e, _ = _two_line(inc[2], inc[3], beta)
+    assert abs(S[0] - S11) < 2e-6
+    assert abs(S[2] - F2 / F2e) < 1e-6
+    assert abs(abs(S[0]) ** 2 + abs(S[2]) ** 2 - 1.0) < 1e-4
 
 
 def test_hankel_self_term_matches_quadrature():
