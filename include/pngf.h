@@ -171,8 +171,12 @@ pngf_status pngf_accept_flip(pngf_ctx* ctx, int32_t pixel);
 pngf_status pngf_accept_flip_noalloc(pngf_ctx* ctx, int32_t pixel);
 
 /*
- * Run direct binary search on the device: up to n_sweeps passes over the
- * pixels; a pass that keeps no flip ends the search (converged).
+ * Run direct binary search on the device (section "Direct binary search
+ * optimization" and Supplementary Fig. 1: flip a tile, evaluate, keep the flip
+ * if the objective improved, else try another; converged when every flip was
+ * tried without improvement), each candidate scored by Eq. 14 and each kept
+ * flip applied by Eq. 9: up to n_sweeps passes over the pixels; a pass that
+ * keeps no flip ends the search (converged).
  *   order     int32 n_sweeps x n_d (device): visiting order of each pass, each
  *             row a permutation of 0..n_d-1; NULL = raster order 0..n_d-1.
  *             FIRST mode keeps the first improving flip in visiting order
@@ -199,10 +203,12 @@ pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order
 
 /*
  * Batched DBS: many independent runs advanced by one kernel launch, one CTA
- * per run at a time.  Independent systems exchange nothing (the paper's
- * section on computational efficiency advances its per-frequency systems side
- * by side for that reason); here they are independent random starts and/or
- * design regions of different sizes sharing one device.
+ * per run at a time.  Independent systems exchange nothing: section
+ * "Computational efficiency" (and Table 1's footnote on multi-frequency
+ * designs) notes that the systems of different frequencies are independent and
+ * can be advanced in parallel; here they are independent random starts and/or
+ * design regions of different sizes sharing one device.  Each run is the
+ * search of pngf_dbs_sweep (section "Direct binary search optimization").
  *   ctxs      host array of n_ctx factored contexts (1 <= n_ctx <= PNGF_BATCH_MAX_RUNS),
  *             one device, one precision and mode, n_d <= PNGF_BATCH_MAX_ND each;
  *             the launch goes to ctxs[0]'s stream, which must order every
@@ -223,19 +229,79 @@ pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n
                                  double* const* trace_f, int32_t trace_cap, int64_t* counters,
                                  void* batch_ws, size_t batch_ws_bytes);
 
-/* Current port amplitudes (c128 n_o, host) and objective (host); synchronizes. */
+/* Current port amplitudes x_obj (c128 n_o, host; Eq. 5, o = c_o + G_od (v .* e))
+ * and objective of the S-parameters (host; the objective forms of
+ * Supplementary Note 9); synchronizes. */
 pngf_status pngf_eval_ports(pngf_ctx* ctx, double* o_host, double* f_host);
 
 /* Copy the current design (uint8 n_d, device). */
 pngf_status pngf_get_design(pngf_ctx* ctx, uint8_t* b);
 
 /*
- * Read back the maintained state (device outputs, any may be NULL):
- *   W c128 n_d x n_d (FP64 precision only, else PNGF_EINVAL if non-NULL),
+ * Read back the maintained state: the quantities the paper keeps between
+ * iterations (C^-1, R and S of Eqs. 11-13, in field form W, T and e) and the
+ * current x_obj (device outputs, any may be NULL):
+ *   W c128 n_d x n_d (FP64 precision only, else PNGF_EINVAL if non-NULL; only
+ *     the upper triangle j >= i is current, the rest is as the search left it),
  *   diag_W c128 n_d, e c128 n_d, T c128 n_o x n_d, o c128 n_o.
  */
 pngf_status pngf_get_state(pngf_ctx* ctx, double* W, double* diag_W, double* e, double* T,
                            double* o);
+
+/*
+ * Gradient of the objective with respect to a continuous density rho_m of
+ * every pixel (v_m = rho_m dv_m; rho = b is the current binary design), from
+ * the maintained state alone (Supplementary Note 5, the chain rule with
+ * Wirtinger derivatives in its elementwise O(N_obj) form, here in the field
+ * form where dx_obj/dv_m = T[:, m] e_m):
+ *   grad    double n_d (device, out): df/drho_m = 2 Re[sum_p (dphi_p/dS_p) scale_p T[p,m] e_m dv_m]
+ *   dodrho  c128 n_o x n_d (device, out) or NULL: do_p/drho_m = T[p,m] e_m dv_m
+ * dphi/dS = w conj(S) (PNGF_OBJ_MAX_WEIGHTED_POWER) or -w (1 - |S|) conj(S)/|S|
+ * (PNGF_OBJ_MIN_INSERTION_LOSS; 0 where S = 0).  Either precision (the mixed
+ * path's e and T are its FP64 copies, current after every call).
+ */
+pngf_status pngf_gradient(pngf_ctx* ctx, double* grad, double* dodrho);
+
+/* Kept flips since the last refresh (host int32); synchronizes.  Part of a
+ * checkpoint: with it, a resumed search refreshes where the original would. */
+pngf_status pngf_get_since_refresh(pngf_ctx* ctx, int32_t* since_refresh);
+
+/*
+ * Checkpoint import: replace the maintained state of a factored context by one
+ * that pngf_get_state / pngf_get_design / pngf_get_since_refresh exported,
+ * possibly from another process (the paper's maintained C^-1, R, S, x_obj of
+ * Eqs. 11-13 between two iterations; the checkpoint itself has no counterpart
+ * in the paper).  Device inputs in the layouts pngf_get_state writes:
+ *   b uint8 n_d, W c128 n_d x n_d (upper triangle read), diag_W, e c128 n_d,
+ *   T c128 n_o x n_d, o c128 n_o; since_refresh >= 0.
+ * FP64 contexts: b and W are required; the context must have been created
+ * with the same inputs and configuration and factored once (at any design);
+ * the resumed search is then bit-for-bit the uninterrupted one.
+ * Mixed contexts: b and W must be NULL and since_refresh < refresh_k; the
+ * context must have been factored at the checkpoint's design; diag W, e, T
+ * and o are replaced, the FP32 inverse is the factor's.
+ * The objective is recomputed from o on the device; v follows b.
+ */
+pngf_status pngf_set_state(pngf_ctx* ctx, const uint8_t* b, const double* W, const double* diag_W,
+                           const double* e, const double* T, const double* o,
+                           int32_t since_refresh);
+
+/*
+ * Failure-detection controls (the paper has no counterpart).
+ *   wait_log2  every bounded device-side wait of this context's later
+ *              launches on other CTAs (grid barriers, the word polls of the
+ *              mixed search) gives up after 2^wait_log2 polls and latches
+ *              PNGF_ETIMEOUT (8..30; 0 = the default 2^24, about ten seconds)
+ *   hold_cta   >= 0: CTA hold_cta of the next pngf_dbs_sweep waits, before it
+ *              takes part in anything grid-wide, on a flag that nothing sets
+ *              (bounded by the same limit); the other CTAs' waits for it run
+ *              out, the call ends with PNGF_ETIMEOUT latched, nothing faults.
+ *              One-shot.  -1 = none.
+ * After a timeout the search state is undefined (restore a snapshot or factor
+ * again); pngf_sync returns and clears the latched status.  Ordered on the
+ * context's stream.
+ */
+pngf_status pngf_set_wait_limit(pngf_ctx* ctx, int32_t wait_log2, int32_t hold_cta);
 
 /* Save the current state inside the workspace / restore it (same stream). */
 pngf_status pngf_snapshot(pngf_ctx* ctx);

@@ -23,6 +23,8 @@ binary design ``b``):
   design, visit tiles one at a time, flip, evaluate, keep the flip if the
   objective improved, otherwise undo it; stop when a whole pass over the tiles
   brings no improvement.  Every visited flip is re-solved from scratch.
+* ``objective_gradient``: the gradient of the objective with respect to a
+  continuous density of every pixel (Supplementary Note 5, field form).
 * ``maintained_inverse`` / ``port_projection``: the plain definitions of the
   quantities a low-rank implementation keeps between iterations (the paper's
   C^-1, R = G_obj C^-1 and S = C^-1 P e_inc of Eqs. 11-12, in field form):
@@ -168,6 +170,40 @@ def port_projection(G: np.ndarray, G_od: np.ndarray, v: np.ndarray) -> np.ndarra
     """T = G_od (I + V W): port response to a unit change of a pixel's current."""
     W = maintained_inverse(G, v)
     return G_od + (G_od * v[None, :]) @ W
+
+
+def objective_gradient(p: Problem, rho: np.ndarray) -> np.ndarray:
+    """df/drho_m of the objective for the density parameterisation v = dv * rho.
+
+    Supplementary Note 5 gives the gradient of a real objective with respect
+    to the design parameters through the chain rule with Wirtinger
+    derivatives, grad f = 2 Re[(df/dx_obj)(dx_obj/dy)(dy/dp)], where the
+    derivative of x_obj with respect to one design entry is the m-th column of
+    R = G_obj C^-1 times the m-th entry of (e_inc - S) (its elementwise
+    form, O(N_obj) work per entry).  In the field form used here
+    (x_obj = o = c_o + G_od V e, M = I - G V, M e = c_d) the same product rule
+    gives do/dv_m = T[:, m] e_m with T = G_od (I + V W), W = M^-1 G; the design
+    parameter is the real density rho_m of pixel m (v_m = rho_m dv_m, so
+    dv_m/drho_m = dv_m; rho in {0, 1} is the binary design).  The objective
+    is f = sum_p phi_p(S_p), S_p = (o_p - off_p) scale_p, with Wirtinger
+    derivatives dphi/dS = w conj(S) for w |S|^2 and
+    -w (1 - |S|) conj(S) / |S| for w (1 - |S|)^2 (0 where S = 0, a cusp).
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    v = p.dv * rho
+    e = solve_field(p.G, p.c_d, v)
+    o = port_amplitudes(p.G_od, p.c_o, v, e)
+    S = s_params(o, p.s_off, p.s_scale)
+    if p.obj_kind == OBJ_MAX_WEIGHTED_POWER:
+        dfdS = p.obj_weights * np.conj(S)
+    elif p.obj_kind == OBJ_MIN_INSERTION_LOSS:
+        a = np.abs(S)
+        dfdS = np.where(a > 0, -p.obj_weights * (1.0 - a) * np.conj(S) / np.where(a > 0, a, 1.0), 0.0)
+    else:
+        raise ValueError(f"unknown objective kind {p.obj_kind}")
+    T = port_projection(p.G, p.G_od, v)
+    dodrho = T * (e * p.dv)[None, :]  # (n_o, n_d): do_p / drho_m
+    return 2.0 * np.real((dfdS * p.s_scale) @ dodrho)
 
 
 @dataclasses.dataclass

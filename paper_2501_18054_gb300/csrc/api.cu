@@ -333,6 +333,54 @@ pngf_status pngf_sync(pngf_ctx* c) {
   return (pngf_status)st;
 }
 
+pngf_status pngf_gradient(pngf_ctx* c, double* grad, double* dodrho) {
+  if (!c || !grad) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  return gradient(c, grad, dodrho);
+}
+
+pngf_status pngf_set_wait_limit(pngf_ctx* c, int32_t wait_log2, int32_t hold_cta) {
+  if (!c) return PNGF_EINVAL;
+  if (wait_log2 != 0 && (wait_log2 < 8 || wait_log2 > 30)) return PNGF_EINVAL;
+  if (hold_cta < -1 || hold_cta >= c->coop_ctas) return PNGF_EINVAL;
+  return set_wait_limit(c, wait_log2 ? (1ull << wait_log2) : 0ull, hold_cta + 1);
+}
+
+pngf_status pngf_get_since_refresh(pngf_ctx* c, int32_t* since_refresh) {
+  if (!c || !since_refresh) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  Control* ctl = at<Control>(c, c->L.ctl);
+  if (cudaMemcpyAsync(since_refresh, &ctl->since_refresh, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PNGF_ECUDA;
+  return PNGF_OK;
+}
+
+pngf_status pngf_set_state(pngf_ctx* c, const uint8_t* b, const double* W, const double* diag_W, const double* e,
+                           const double* T, const double* o, int32_t since_refresh) {
+  if (!c || !diag_W || !e || !T || !o || since_refresh < 0) return PNGF_EINVAL;
+  if (!c->factored) return PNGF_ENOTFACTORED;
+  const bool fp64 = c->cfg.precision == PNGF_FP64;
+  if (fp64 ? (!W || !b) : (W || b)) return PNGF_EINVAL;
+  if (!fp64 && c->cfg.refresh_k > 0 && since_refresh >= c->cfg.refresh_k) return PNGF_EINVAL;
+  const size_t n = c->cfg.n_d, n_o = c->cfg.n_o, cs = sizeof(c128);
+  cudaStream_t s = c->stream;
+  if (fp64) {
+    if (cudaMemcpy2DAsync(at<c128>(c, c->L.W), (size_t)c->L.ldw * cs, W, n * cs, n * cs, n,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(at<uint8_t>(c, c->L.b), b, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return PNGF_ECUDA;
+  }
+  if (cudaMemcpyAsync(at<c128>(c, c->L.diag), diag_W, n * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(at<c128>(c, c->L.e), e, n * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpy2DAsync(at<c128>(c, c->L.T), (size_t)c->L.ldt * cs, T, n * cs, n * cs, n_o,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(&at<Control>(c, c->L.ctl)->o[0], o, n_o * cs, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PNGF_ECUDA;
+  return import_finish(c, since_refresh);
+}
+
 const char* pngf_status_string(pngf_status s) {
   switch (s) {
     case PNGF_OK: return "ok";

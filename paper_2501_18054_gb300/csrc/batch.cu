@@ -15,7 +15,8 @@
 // sequential trajectory as scoring all remaining positions, with less
 // speculative work when flips are kept often).
 #include <cstdio>
-#include <vector>
+#include <memory>
+#include <new>
 
 #include "flush_tc.cuh"
 
@@ -288,6 +289,20 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   if (use_tc) tc_teardown(tcs, tc_failed);
 }
 
+// The per-run argument table is written by the device from kernel parameters
+// (chunks of the table passed by value), so that no host buffer has to outlive
+// the call: a stream capture records the values themselves.
+constexpr int kArgChunk = 30000 / (int)sizeof(SweepArgs);
+struct ArgChunk {
+  SweepArgs a[kArgChunk];
+  int count;
+};
+static_assert(kArgChunk >= 1 && sizeof(ArgChunk) <= 32000, "kernel parameter space");
+
+__global__ void write_args_kernel(const ArgChunk ch, SweepArgs* __restrict__ dst) {
+  for (int i = threadIdx.x; i < ch.count; i += blockDim.x) dst[i] = ch.a[i];
+}
+
 }  // namespace
 
 size_t batch_workspace_bytes(int n_runs) { return ((size_t)n_runs * sizeof(SweepArgs) + 255) / 256 * 256; }
@@ -296,22 +311,27 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
                             int32_t* const* traces, double* const* trace_f, int32_t trace_cap, int64_t* counters,
                             void* ws, size_t ws_bytes) {
   pngf_ctx* c0 = ctxs[0];
-  std::vector<SweepArgs> host(n_runs);
+  SweepArgs* table = static_cast<SweepArgs*>(ws);
+  std::unique_ptr<ArgChunk> ch(new (std::nothrow) ArgChunk());
+  if (!ch) return PNGF_ENOMEM;
   int max_n = 0;
-  for (int r = 0; r < n_runs; ++r) {
-    SweepArgs a = make_args(ctxs[r]);
-    a.n_sweeps = n_sweeps;
-    a.order = orders ? orders[r] : nullptr;
-    a.trace = traces ? traces[r] : nullptr;
-    a.trace_f = trace_f ? trace_f[r] : nullptr;
-    a.trace_cap = trace_cap;
-    a.counters = counters ? counters + 8 * (size_t)r : nullptr;
-    host[r] = a;
-    if (a.n > max_n) max_n = a.n;
+  for (int r0 = 0; r0 < n_runs; r0 += kArgChunk) {
+    ch->count = n_runs - r0 < kArgChunk ? n_runs - r0 : kArgChunk;
+    for (int i = 0; i < ch->count; ++i) {
+      const int r = r0 + i;
+      SweepArgs a = make_args(ctxs[r]);
+      a.n_sweeps = n_sweeps;
+      a.order = orders ? orders[r] : nullptr;
+      a.trace = traces ? traces[r] : nullptr;
+      a.trace_f = trace_f ? trace_f[r] : nullptr;
+      a.trace_cap = trace_cap;
+      a.counters = counters ? counters + 8 * (size_t)r : nullptr;
+      ch->a[i] = a;
+      if (a.n > max_n) max_n = a.n;
+    }
+    write_args_kernel<<<1, 128, 0, c0->stream>>>(*ch, table + r0);
+    if (cudaGetLastError() != cudaSuccess) return PNGF_ECUDA;
   }
-  if (cudaMemcpyAsync(ws, host.data(), (size_t)n_runs * sizeof(SweepArgs), cudaMemcpyHostToDevice, c0->stream) !=
-      cudaSuccess)
-    return PNGF_ECUDA;
   const bool mixed = c0->cfg.precision == PNGF_MIXED;
   size_t smem = mixed ? (kFlushSmem > (size_t)tc_fold_smem(1) ? kFlushSmem : (size_t)tc_fold_smem(1)) : (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

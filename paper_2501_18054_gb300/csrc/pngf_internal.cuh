@@ -99,12 +99,16 @@ constexpr int kRecordBytes = 512;
 // Device-resident, inside the workspace.
 struct Control {
   int status;            // latched pngf_status (first error wins)
-  int pad0;
+  int hold_cta;          // failure-detection test hook: CTA hold_cta - 1 of the next sweep waits
+                         // (bounded) for hold_flag before it joins the others; 0 = none
   unsigned int bar_count;   // grid barrier arrivals
   unsigned int bar_gen;     // grid barrier generation
   long long counters[8];    // see pngf_dbs_sweep
   unsigned long long sel[3];  // FIRST mode: per-round minimum of (position << 10 | cta), 3 rotating cells
   long long phase_cycles[16];  // SM cycles of CTA 0 per sweep phase (last sweep)
+  unsigned long long spin_limit;  // polls before a bounded device wait gives up (0 = default)
+  int hold_flag;            // never set: the held CTA's wait runs out
+  int pad1;
   double f;                 // current objective
   int factored;
   int n_acc_total;          // accepted flips since the last factor / restore
@@ -176,6 +180,10 @@ pngf_status run_sweep(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* 
 pngf_status score_flips(pngf_ctx* c, const int32_t* pixels, int n, double* f_new, double* o_new);
 pngf_status accept_flip(pngf_ctx* c, int pixel);
 pngf_status accept_flip_noalloc(pngf_ctx* c, int pixel);
+pngf_status set_wait_limit(pngf_ctx* c, unsigned long long polls, int hold_plus1);
+pngf_status import_finish(pngf_ctx* c, int since_refresh);
+// gradient.cu
+pngf_status gradient(pngf_ctx* c, double* grad, double* dodrho);
 int sweep_grid_size(pngf_ctx* c);
 
 inline pngf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PNGF_OK : PNGF_ECUDA; }

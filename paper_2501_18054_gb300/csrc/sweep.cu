@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
   const long long E = (long long)n * (n + 1) / 2;
   const long long eb = E * cta / P, ee = E * (cta + 1) / P;
   Control* ctl = a.ctl;
+  hold_if_asked(ctl);
   // search state shared by the CTA (identical in every CTA: each one derives it
   // from the same data in the same order)
   __shared__ c128 s_o[kMaxPorts];
@@ -341,7 +342,36 @@ __global__ void __launch_bounds__(kThreads) accept_update_kernel(SweepArgs a, co
   rank1_upper(a.W, n, a.ldw, a.cbuf, pv.alpha, E * cta / P, E * (cta + 1) / P);
 }
 
+__global__ void set_wait_kernel(Control* ctl, unsigned long long polls, int hold_plus1) {
+  ctl->spin_limit = polls;
+  ctl->hold_cta = hold_plus1;
+  ctl->hold_flag = 0;
+}
+
+// after an imported state: v from b, f from o, the refresh phase
+__global__ void import_finish_kernel(SweepArgs a, int since_refresh) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x)
+    a.v[j] = a.b[j] ? a.dv[j] : mk(0.0, 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->f = objective_of(a.op, a.ctl->o);
+    a.ctl->since_refresh = since_refresh;
+  }
+}
+
 }  // namespace
+
+pngf_status set_wait_limit(pngf_ctx* c, unsigned long long polls, int hold_plus1) {
+  set_wait_kernel<<<1, 1, 0, c->stream>>>(at<Control>(c, c->L.ctl), polls, hold_plus1);
+  return cuda_status(cudaGetLastError());
+}
+
+pngf_status import_finish(pngf_ctx* c, int since_refresh) {
+  SweepArgs a = make_args(c);
+  int blocks = (c->cfg.n_d + 255) / 256;
+  if (blocks > c->n_sm) blocks = c->n_sm;
+  import_finish_kernel<<<blocks, 256, 0, c->stream>>>(a, since_refresh);
+  return cuda_status(cudaGetLastError());
+}
 
 // active-pixel list of the refresh residual, then the staging of the correction
 static size_t fp64_smem(int n) {

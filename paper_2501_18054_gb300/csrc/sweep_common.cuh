@@ -9,7 +9,15 @@ namespace pngf {
 namespace {
 
 constexpr int kThreads = 512;
-constexpr unsigned long long kSpinLimit = 1ull << 24;  // ~seconds with the 128 ns back-off
+// Default bound of every device-side wait on other CTAs: 2^24 polls, each an L2
+// round trip plus (after the first few) a 32 ns back-off, on the order of ten
+// seconds.  pngf_set_wait_limit sets a context's own bound (Control::spin_limit).
+constexpr unsigned long long kSpinLimit = 1ull << 24;
+
+__device__ __forceinline__ unsigned long long spin_limit_of(const Control* ctl) {
+  const unsigned long long l = *reinterpret_cast<const volatile unsigned long long*>(&ctl->spin_limit);
+  return l ? l : kSpinLimit;
+}
 
 struct SweepArgs {
   int n, n_o, ldw, ldt;
@@ -90,11 +98,12 @@ __device__ bool grid_sync(Control* ctl) {
     int ok = 1;
     fence_acq_rel_gpu();  // release: this CTA's writes before its arrival
     const unsigned P = gridDim.x;
+    const unsigned long long lim = spin_limit_of(ctl);
     const unsigned old = atomicAdd(&ctl->bar_count, 1u);
     const unsigned target = (old / P + 1) * P;
     unsigned long long it = 0;
     while ((int)(ld_volatile(&ctl->bar_count) - target) < 0) {
-      if (++it > kSpinLimit) {
+      if (++it > lim) {
         latch_status(ctl, PNGF_ETIMEOUT);
         ok = 0;
         break;
@@ -106,6 +115,22 @@ __device__ bool grid_sync(Control* ctl) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Test hook of the timeout path (pngf_set_wait_limit): CTA hold_cta - 1 waits
+// on a flag that nothing sets, bounded by a longer wait than the others' own
+// limit, before it takes part in anything grid-wide; the other CTAs' bounded
+// waits for it run out and latch PNGF_ETIMEOUT.  One-shot: the hold is cleared.
+__device__ void hold_if_asked(Control* ctl) {
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&ctl->hold_cta) == (int)blockIdx.x + 1) {
+    const unsigned long long lim = 4 * spin_limit_of(ctl);
+    for (unsigned long long it = 0; it < lim; ++it) {
+      if (*reinterpret_cast<volatile int*>(&ctl->hold_flag) != 0) break;
+      __nanosleep(256);
+    }
+    ctl->hold_cta = 0;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- FIRST-mode selection cells

@@ -132,12 +132,13 @@ __device__ __forceinline__ dd improve_bound(dd f, dd tau) {
 }
 
 // waits (bounded) for CTA q's word of round `seq`; returns its key
-__device__ __forceinline__ long long poll_word(const unsigned long long* w, unsigned seq, bool& ok) {
+__device__ __forceinline__ long long poll_word(const unsigned long long* w, unsigned seq, bool& ok,
+                                               unsigned long long lim) {
   unsigned long long it = 0;
   for (;;) {
     unsigned long long v = *reinterpret_cast<const volatile unsigned long long*>(w);
     if ((unsigned)(v >> kSeqShift) == seq) return (long long)(v & kKeyMask);
-    if (++it > kSpinLimit) {
+    if (++it > lim) {
       ok = false;
       return kNoCand;
     }
@@ -154,6 +155,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   const int pb = (int)((long long)n * cta / P), pe = (int)((long long)n * (cta + 1) / P);
   const int own = pe - pb;
   Control* ctl = a.ctl;
+  const unsigned long long spin_lim = spin_limit_of(ctl);
+  hold_if_asked(ctl);
   // own-pixel state (thread jl < own scores pixel pb + jl)
   // (double-words, so that the per-flip chain runs on the FP32 pipe; dv itself stays FP64)
   cdd* s_T = reinterpret_cast<cdd*>(dyn_smem);  // [kMaxPorts][kOwnMax], T'_p,j = T_p,j scale_p
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       long long kq = kNoCand;
       if (tid < P) {
         bool ok = true;
-        kq = poll_word(words + (size_t)tid * kSlotStride, seq, ok);
+        kq = poll_word(words + (size_t)tid * kSlotStride, seq, ok, spin_lim);
         if (!ok) {
           s_fail = 1;
           latch_status(ctl, PNGF_ETIMEOUT);

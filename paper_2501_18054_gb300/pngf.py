@@ -83,6 +83,10 @@ def lib() -> ctypes.CDLL:
             "pngf_eval_ports": (st, [_P, _P, _P]),
             "pngf_get_design": (st, [_P, _P]),
             "pngf_get_state": (st, [_P, _P, _P, _P, _P, _P]),
+            "pngf_gradient": (st, [_P, _P, _P]),
+            "pngf_get_since_refresh": (st, [_P, _P]),
+            "pngf_set_state": (st, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
+            "pngf_set_wait_limit": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
             "pngf_snapshot": (st, [_P]),
             "pngf_restore": (st, [_P]),
             "pngf_sync": (st, [_P]),
@@ -104,7 +108,8 @@ def exported_symbols() -> list:
     names = []
     for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
               "pngf_accept_flip_noalloc", "pngf_batch_workspace_size", "pngf_dbs_sweep_batch",
-              "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state", "pngf_snapshot",
+              "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state",
+              "pngf_gradient", "pngf_get_since_refresh", "pngf_set_state", "pngf_set_wait_limit", "pngf_snapshot",
               "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
         if hasattr(L, n):
             names.append(n)
@@ -196,6 +201,25 @@ def pngf_get_design(ctx: int, b: int) -> None:
 def pngf_get_state(ctx: int, W: Optional[int], diag_W: Optional[int], e: Optional[int], T: Optional[int],
                    o: Optional[int]) -> None:
     _check(lib().pngf_get_state(ctx, W, diag_W, e, T, o), "pngf_get_state")
+
+
+def pngf_gradient(ctx: int, grad: int, dodrho: Optional[int]) -> None:
+    _check(lib().pngf_gradient(ctx, grad, dodrho), "pngf_gradient")
+
+
+def pngf_get_since_refresh(ctx: int) -> int:
+    out = ctypes.c_int32(0)
+    _check(lib().pngf_get_since_refresh(ctx, ctypes.cast(ctypes.byref(out), _P)), "pngf_get_since_refresh")
+    return int(out.value)
+
+
+def pngf_set_state(ctx: int, b: Optional[int], W: Optional[int], diag_W: int, e: int, T: int, o: int,
+                   since_refresh: int) -> None:
+    _check(lib().pngf_set_state(ctx, b, W, diag_W, e, T, o, int(since_refresh)), "pngf_set_state")
+
+
+def pngf_set_wait_limit(ctx: int, wait_log2: int, hold_cta: int) -> None:
+    _check(lib().pngf_set_wait_limit(ctx, int(wait_log2), int(hold_cta)), "pngf_set_wait_limit")
 
 
 def pngf_snapshot(ctx: int) -> None:
@@ -346,6 +370,43 @@ class DbsContext:
         if W is not None:
             out["W"] = W.cpu().numpy()
         return out
+
+    def gradient(self, want_dodrho: bool = False):
+        """df/drho at the current design (pngf_gradient), as host arrays."""
+        torch = self.torch
+        g = torch.empty(self.n_d, dtype=torch.float64, device=self.device)
+        d = torch.empty((self.n_o, self.n_d), dtype=torch.complex128, device=self.device) if want_dodrho else None
+        pngf_gradient(self.ctx, g.data_ptr(), d.data_ptr() if d is not None else None)
+        self.stream.synchronize()
+        return (g.cpu().numpy(), d.cpu().numpy()) if want_dodrho else g.cpu().numpy()
+
+    def checkpoint(self) -> dict:
+        """The maintained state as host arrays (pngf_get_state / _design / _since_refresh)."""
+        st = self.state(with_W=self.cfg.precision == PNGF_FP64)
+        st["b"] = self.design()
+        st["since_refresh"] = pngf_get_since_refresh(self.ctx)
+        return st
+
+    def set_state(self, ck: dict) -> None:
+        """Import a checkpoint() (pngf_set_state); FP64 contexts take b and W too."""
+        torch = self.torch
+        fp64 = self.cfg.precision == PNGF_FP64
+
+        def dev(x, dt):
+            return torch.as_tensor(np.ascontiguousarray(x)).to(self.device, dt)
+
+        keep = dict(d=dev(ck["diag"], torch.complex128), e=dev(ck["e"], torch.complex128),
+                    T=dev(ck["T"], torch.complex128), o=dev(ck["o"], torch.complex128))
+        if fp64:
+            keep["W"] = dev(ck["W"], torch.complex128)
+            keep["b"] = dev(ck["b"], torch.uint8)
+        pngf_set_state(self.ctx, keep["b"].data_ptr() if fp64 else None, keep["W"].data_ptr() if fp64 else None,
+                       keep["d"].data_ptr(), keep["e"].data_ptr(), keep["T"].data_ptr(), keep["o"].data_ptr(),
+                       int(ck["since_refresh"]))
+        self.stream.synchronize()
+
+    def set_wait_limit(self, wait_log2: int, hold_cta: int = -1) -> None:
+        pngf_set_wait_limit(self.ctx, wait_log2, hold_cta)
 
     def phase_cycles(self) -> np.ndarray:
         return pngf_get_phase_cycles(self.ctx)

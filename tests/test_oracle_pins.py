@@ -255,3 +255,69 @@ def test_planted_s_param_mistakes_are_caught(fdfd64, metal128, monkeypatch):
             worst = max(worst, np.max(np.abs(S - Sf)) / np.max(np.abs(Sf)))
         assert worst > 1e-6, what
     monkeypatch.undo()
+
+
+def _grad_fd(p, rho, ms, h=1e-5):
+    out = []
+    for m in ms:
+        r1, r2 = rho.copy(), rho.copy()
+        r1[m] += h
+        r2[m] -= h
+        out.append((O.evaluate(p, r1).f - O.evaluate(p, r2).f) / (2 * h))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", [O.OBJ_MAX_WEIGHTED_POWER, O.OBJ_MIN_INSERTION_LOSS])
+@pytest.mark.parametrize("fractional", [False, True])
+def test_gradient_equals_finite_differences(fdfd64, kind, fractional):
+    """objective_gradient equals central differences of the pinned evaluate
+    at a binary and at a fractional density (v = dv * rho)."""
+    p = O.Problem.from_case(fdfd64)
+    p.obj_kind = kind
+    rng = np.random.default_rng(7)
+    rho = W.random_design(fdfd64.n_d, 4).astype(np.float64)
+    if fractional:
+        rho = rng.random(fdfd64.n_d)
+    g = O.objective_gradient(p, rho)
+    ms = rng.choice(fdfd64.n_d, 12, replace=False)
+    fd = _grad_fd(p, rho, ms)
+    assert np.max(np.abs(g[ms] - fd)) <= 1e-6 * np.max(np.abs(fd))
+    assert np.max(np.abs(fd)) > 1e-3
+
+
+def test_gradient_one_pixel_closed_form(fdfd64):
+    """N_d = 1: S(rho) = (c_o + G_od rho dv c/(1 - g rho dv) - off) scale, so
+    dS/drho = scale G_od dv c / (1 - g rho dv)^2 and d|S_2|^2/drho = 2 Re(conj(S_2) dS_2/drho)."""
+    s = fdfd64.sub_case([57])
+    p = O.Problem.from_case(s)
+    g, c, dv = s.G_dd[0, 0], s.c_d[0], s.dv[0]
+    for rho in (0.0, 0.3, 1.0):
+        den = 1.0 - g * rho * dv
+        S = (s.c_o + s.G_od[:, 0] * rho * dv * c / den - s.s_off) * s.s_scale
+        dS = s.s_scale * s.G_od[:, 0] * dv * c / den ** 2
+        want = float(np.sum(s.obj_weights * 2.0 * np.real(np.conj(S) * dS)))
+        got = O.objective_gradient(p, np.array([rho]))[0]
+        assert abs(got - want) <= 1e-12 * abs(want)
+
+
+def test_planted_gradient_mistakes_are_caught(fdfd64, monkeypatch):
+    """Plausible slips in the gradient's chain rule fail the finite-difference pin."""
+    p = O.Problem.from_case(fdfd64)
+    rho = W.random_design(fdfd64.n_d, 4).astype(np.float64)
+    ms = np.arange(0, 100, 9)
+    fd = _grad_fd(p, rho, ms)
+    real = O.pngf_oracle.port_projection
+    plants = {
+        "T without the V W term": lambda G, God, v: God.copy(),
+        "transposed W in T": lambda G, God, v: God + (God * v[None, :]) @ O.maintained_inverse(G, v).T.conj(),
+        "T scaled by V": lambda G, God, v: real(G, God, v) * v[None, :],
+    }
+    for what, bad in plants.items():
+        monkeypatch.setattr(O.pngf_oracle, "port_projection", bad)
+        g = O.objective_gradient(p, rho)
+        assert np.max(np.abs(g[ms] - fd)) > 1e-3 * np.max(np.abs(fd)), what
+    monkeypatch.undo()
+    monkeypatch.setattr(O.pngf_oracle, "s_params", lambda o, off, sc: (o - off) * np.conj(sc))
+    g = O.objective_gradient(p, rho)
+    monkeypatch.undo()
+    assert np.max(np.abs(g[ms] - fd)) > 1e-3 * np.max(np.abs(fd)), "conjugated scale"
