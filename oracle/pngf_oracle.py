@@ -23,6 +23,10 @@ binary design ``b``):
   design, visit tiles one at a time, flip, evaluate, keep the flip if the
   objective improved, otherwise undo it; stop when a whole pass over the tiles
   brings no improvement.  Every visited flip is re-solved from scratch.
+* ``dbs_tiles``: DBS whose candidates flip a whole tile (several pixels at
+  once, the paper's rank-M flips) on one or several systems that share the
+  design (the paper's per-frequency systems), the per-system objectives
+  combined into one by a mean or a min-max rule; every candidate re-solved.
 * ``objective_gradient``: the gradient of the objective with respect to a
   continuous density of every pixel (Supplementary Note 5, field form).
 * ``maintained_inverse`` / ``port_projection``: the plain definitions of the
@@ -55,6 +59,8 @@ OBJ_MAX_WEIGHTED_POWER = 0
 OBJ_MIN_INSERTION_LOSS = 1
 FIRST_IMPROVEMENT = 0
 BEST_IMPROVEMENT = 1
+COMBINE_MEAN = 0   # arithmetic mean of the per-system objectives
+COMBINE_WORST = 1  # min-max: the worst system (lowest maximised / highest minimised objective)
 
 
 def system_matrix(G: np.ndarray, v: np.ndarray) -> np.ndarray:
@@ -280,3 +286,101 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
         if not any_accept or (max_evals is not None and n_evals >= max_evals):
             break
     return DbsResult(accepted, b, f, cur.o, cur.S, n_evals, sweeps_done, float(min_margin), margins)
+
+
+# ---------------------------------------------------------------- tile flips and several systems
+def combined_objective(fs, kind: int, combine: int) -> float:
+    """One scalar from the objectives of several systems (Supplementary Note 9:
+    the per-frequency objectives are combined by a mean or a min-max rule)."""
+    fs = np.asarray(fs, dtype=np.float64)
+    if combine == COMBINE_MEAN:
+        return float(np.mean(fs))
+    if combine == COMBINE_WORST:
+        return float(np.min(fs)) if kind == OBJ_MAX_WEIGHTED_POWER else float(np.max(fs))
+    raise ValueError(f"unknown combine rule {combine}")
+
+
+def flip_tile(b: np.ndarray, tile) -> np.ndarray:
+    """The design with every pixel of one tile flipped (negative entries pad a tile)."""
+    b2 = np.asarray(b, dtype=np.uint8).copy()
+    for k in tile:
+        if k >= 0:
+            b2[k] ^= 1
+    return b2
+
+
+def tile_candidate_objectives(problems, b, tiles, combine: int) -> np.ndarray:
+    """Combined objective after flipping each tile alone, re-solved from scratch
+    in every system; a candidate singular in any system gets NaN."""
+    out = np.empty(len(tiles), dtype=np.float64)
+    for i, tile in enumerate(tiles):
+        b2 = flip_tile(b, tile)
+        try:
+            out[i] = combined_objective([evaluate(p, b2).f for p in problems], problems[0].obj_kind, combine)
+        except np.linalg.LinAlgError:
+            out[i] = np.nan
+    return out
+
+
+def dbs_tiles(problems, b0: np.ndarray, tiles, order: np.ndarray, tau: float = 1e-9,
+              mode: int = FIRST_IMPROVEMENT, combine: int = COMBINE_MEAN) -> DbsResult:
+    """Direct binary search over tile flips on one or several systems sharing the design.
+
+    The paper's DBS flips a tile -- the M unknowns of a block of cells, and in
+    its designs 2 to 4 symmetry-tied tiles at once ("Low-rank update
+    evaluation"; Methods, "Optimization parameters") -- and its multi-frequency
+    designs evaluate one system per frequency on the same design ("Computational
+    efficiency") with the per-frequency objectives combined into one scalar
+    (Supplementary Note 9).  Here every candidate flips all pixels of one tile
+    (a row of ``tiles``; negative entries pad), every system is re-solved from
+    scratch, and the combined objective decides: FIRST keeps the first
+    improving tile of the visiting order (rows of ``order`` are permutations of
+    the tile indices), BEST the best improving tile (ties -> lowest tile index).
+    ``trace`` entries are (sweep, position, tile, combined objective after).
+    """
+    kind = problems[0].obj_kind
+    b = np.asarray(b0, dtype=np.uint8).copy()
+
+    def fcomb(bb):
+        evs = [evaluate(p, bb) for p in problems]
+        return combined_objective([ev.f for ev in evs], kind, combine), evs
+
+    f, evs = fcomb(b)
+    accepted: List[tuple] = []
+    n_evals, sweeps_done, min_margin = 0, 0, np.inf
+    order = np.atleast_2d(np.asarray(order))
+    n_t = len(tiles)
+    for s in range(order.shape[0]):
+        any_accept = False
+        if mode == FIRST_IMPROVEMENT:
+            for t, ti in enumerate(order[s]):
+                b2 = flip_tile(b, tiles[ti])
+                n_evals += 1
+                try:
+                    f2, evs2 = fcomb(b2)
+                except np.linalg.LinAlgError:
+                    continue
+                margin = improvement(f2, f, kind) - tau * max(abs(f), 1e-30)
+                min_margin = min(min_margin, abs(margin))
+                if margin > 0:
+                    b, f, evs = b2, f2, evs2
+                    accepted.append((s, t, int(ti), f))
+                    any_accept = True
+        else:
+            fs = tile_candidate_objectives(problems, b, tiles, combine)
+            n_evals += n_t
+            gains = np.array([improvement(x, f, kind) if np.isfinite(x) else -np.inf for x in fs])
+            m = gains - tau * max(abs(f), 1e-30)
+            min_margin = min(min_margin, float(np.min(np.abs(m[np.isfinite(m)]))))
+            best = int(np.argmax(gains))
+            if m[best] > 0:
+                b = flip_tile(b, tiles[best])
+                f, evs = fcomb(b)
+                accepted.append((s, 0, best, f))
+                any_accept = True
+        sweeps_done += 1
+        if not any_accept:
+            break
+    res = DbsResult(accepted, b, f, evs[0].o, evs[0].S, n_evals, sweeps_done, float(min_margin))
+    res.o_all = [ev.o for ev in evs]
+    return res

@@ -186,6 +186,11 @@ class FdfdSpec:
     obj_weights: tuple = (0.0, 1.0)
     ny: Optional[int] = None  # grid extent along y (default n)
     npml_y: Optional[int] = None  # PML along y (default npml; 0 = Dirichlet walls)
+    lambda_cells: float = LAMBDA_CELLS  # free-space wavelength in cells (one frequency)
+
+
+def _at_wavelength(spec: "FdfdSpec", lam: float) -> "FdfdSpec":
+    return dataclasses.replace(spec, name=f"{spec.name}_l{lam:g}", lambda_cells=float(lam))
 
 
 SPECS = {
@@ -202,6 +207,12 @@ SPECS = {
                         slab=(120, 136, 2.2), source="mode", source_x=20, ports_x=(24, 232),
                         port_kind="mode", norm="reference"),
 }
+# the free-space device at two more frequencies (wavelengths of 19 and 21 cells):
+# the systems of a multi-frequency design on one shared pixel layout
+SPECS["fdfd64_l19"] = _at_wavelength(SPECS["fdfd64"], 19)
+SPECS["fdfd64_l21"] = _at_wavelength(SPECS["fdfd64"], 21)
+SPECS["fdfd128_metal_l19"] = _at_wavelength(SPECS["fdfd128_metal"], 19)
+SPECS["fdfd128_metal_l21"] = _at_wavelength(SPECS["fdfd128_metal"], 21)
 
 
 def _ny(spec: FdfdSpec) -> int:
@@ -225,6 +236,10 @@ def _design_nodes(spec: FdfdSpec):
     return (ix * _ny(spec) + iy).ravel()  # raster order: k = (ix-x0)*ddy + (iy-y0)
 
 
+def _k(spec: FdfdSpec) -> float:
+    return 2.0 * np.pi / spec.lambda_cells
+
+
 def _source_and_ports(spec: FdfdSpec, eps: np.ndarray):
     n, ny = spec.n, _ny(spec)
     s = np.zeros((n, ny), dtype=np.complex128)
@@ -233,14 +248,14 @@ def _source_and_ports(spec: FdfdSpec, eps: np.ndarray):
         y0, y1 = spec.source_y
         s[spec.source_x, y0:y1] = 1.0
     else:
-        phi, _ = slab_mode(eps[spec.source_x, :])
+        phi, _ = slab_mode(eps[spec.source_x, :], _k(spec))
         s[spec.source_x, :] = phi
     for p, xp in enumerate(spec.ports_x):
         if spec.port_kind == "line":
             y0, y1 = spec.source_y
             ports[p, xp, y0:y1] = 1.0 / (y1 - y0)
         else:
-            phi, _ = slab_mode(eps[xp, :])
+            phi, _ = slab_mode(eps[xp, :], _k(spec))
             ports[p, xp, :] = phi
     return s.ravel(), ports.reshape(len(spec.ports_x), -1)
 
@@ -249,7 +264,7 @@ def solve_full(spec: FdfdSpec, eps: np.ndarray):
     """Direct sparse solve of the full structure: returns (E, port amplitudes)."""
     import scipy.sparse.linalg as spl
 
-    A, sxy = helmholtz_operator(eps, spec.npml, npml_y=spec.npml_y)
+    A, sxy = helmholtz_operator(eps, spec.npml, _k(spec), npml_y=spec.npml_y)
     s, Pi = _source_and_ports(spec, _eps_grid(spec))
     E = spl.splu(A.tocsc()).solve(-(sxy * s))
     return E, Pi @ E
@@ -274,9 +289,9 @@ def _build_fdfd(spec: FdfdSpec) -> Case:
     import scipy.sparse.linalg as spl
 
     n = spec.n * _ny(spec)
-    k = K_CELL
+    k = _k(spec)
     eps = _eps_grid(spec)
-    A, sxy = helmholtz_operator(eps, spec.npml, npml_y=spec.npml_y)
+    A, sxy = helmholtz_operator(eps, spec.npml, k, npml_y=spec.npml_y)
     dnodes = _design_nodes(spec)
     n_d = len(dnodes)
     mask = np.zeros(n, dtype=bool)
@@ -314,7 +329,7 @@ def _build_fdfd(spec: FdfdSpec) -> Case:
     else:
         # reference: the same source in the unbroken waveguide gives the incident mode amplitude
         eps_ref = _eps_grid(spec, with_slab_through_design=True)
-        A_ref, _ = helmholtz_operator(eps_ref, spec.npml, npml_y=spec.npml_y)
+        A_ref, _ = helmholtz_operator(eps_ref, spec.npml, k, npml_y=spec.npml_y)
         E_ref = spl.splu(A_ref.tocsc()).solve(-(sxy * s))
         a = Pi @ E_ref
         s_off = np.array([a[0]] + [0.0] * (len(a) - 1), dtype=np.complex128)
@@ -399,6 +414,36 @@ def random_design(n_d: int, seed: int, p: float = 0.5) -> np.ndarray:
     """b_0 ~ Bernoulli(p) per pixel, numpy PCG64(seed); uint8."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return (rng.random(n_d) < p).astype(np.uint8)
+
+
+def square_tiles(side_x: int, side_y: int, t: int) -> np.ndarray:
+    """Tiles of t x t pixels over a side_x x side_y region in raster order
+    (pixel k = x * side_y + y); (side_x/t * side_y/t, t*t) int32."""
+    assert side_x % t == 0 and side_y % t == 0
+    out = []
+    for tx in range(side_x // t):
+        for ty in range(side_y // t):
+            out.append([(tx * t + i) * side_y + ty * t + j for i in range(t) for j in range(t)])
+    return np.asarray(out, dtype=np.int32)
+
+
+def mirror_tied_tiles(side_x: int, side_y: int, t: int) -> np.ndarray:
+    """t x t tiles tied to their mirror image about the region's centre line
+    y -> side_y - 1 - y (a design kept symmetric, as the paper's designs flip 2
+    or 4 symmetry-tied tiles at once); a tile on the centre line is its own
+    image and is padded with -1.  Shape (n_tied, 2*t*t) int32."""
+    sq = square_tiles(side_x, side_y, t)
+    nty = side_y // t
+    out = []
+    for tx in range(side_x // t):
+        for ty in range((nty + 1) // 2):
+            a = sq[tx * nty + ty]
+            m = nty - 1 - ty
+            if m == ty:
+                out.append(np.concatenate([a, -np.ones_like(a)]))
+            else:
+                out.append(np.concatenate([a, sq[tx * nty + m]]))
+    return np.asarray(out, dtype=np.int32)
 
 
 def raster_order(n_d: int, n_sweeps: int) -> np.ndarray:

@@ -321,3 +321,88 @@ def test_planted_gradient_mistakes_are_caught(fdfd64, monkeypatch):
     g = O.objective_gradient(p, rho)
     monkeypatch.undo()
     assert np.max(np.abs(g[ms] - fd)) > 1e-3 * np.max(np.abs(fd)), "conjugated scale"
+
+
+# ---------------------------------------------------------------- tile flips on several systems
+def test_combined_objective_rules():
+    assert O.combined_objective([1.0, 3.0], O.OBJ_MAX_WEIGHTED_POWER, O.COMBINE_MEAN) == 2.0
+    assert O.combined_objective([1.0, 3.0], O.OBJ_MAX_WEIGHTED_POWER, O.COMBINE_WORST) == 1.0
+    assert O.combined_objective([1.0, 3.0], O.OBJ_MIN_INSERTION_LOSS, O.COMBINE_WORST) == 3.0
+
+
+def test_single_pixel_tiles_reduce_to_pixel_dbs(fdfd64):
+    """Tiles of one pixel on one system: the same trajectory as the pixel DBS
+    (itself pinned by brute force above)."""
+    p = O.Problem.from_case(fdfd64)
+    b0 = W.random_design(fdfd64.n_d, 3)
+    order = W.shuffled_order(fdfd64.n_d, 3, seed=2)
+    ref = O.dbs(p, b0, order, tau=1e-9)
+    tiles = np.arange(fdfd64.n_d, dtype=np.int32)[:, None]
+    for combine in (O.COMBINE_MEAN, O.COMBINE_WORST):
+        res = O.dbs_tiles([p], b0, tiles, order, tau=1e-9, combine=combine)
+        assert [a[:3] for a in res.accepted] == [a[:3] for a in ref.accepted]
+        assert res.f == ref.f and np.array_equal(res.b, ref.b)
+    # two copies of one system under the mean: the same search again
+    res2 = O.dbs_tiles([p, p], b0, tiles, order, tau=1e-9)
+    assert [a[:3] for a in res2.accepted] == [a[:3] for a in ref.accepted]
+
+
+@pytest.fixture(scope="module")
+def tiny_two_freq(fdfd64):
+    idx = [10 * x + y for x in range(3, 6) for y in range(3, 7)]  # 12 pixels, a 3 x 4 block
+    l19 = W.get_case("fdfd64_l19")
+    subs = [fdfd64.sub_case(idx), l19.sub_case(idx)]
+    probs = [O.Problem.from_case(s) for s in subs]
+    tables = [_enumerate(p) for p in probs]
+    # pairs of vertically adjacent pixels of the block: 6 tiles of 2
+    tiles = np.array([[4 * x + y, 4 * x + y + 1] for x in range(3) for y in (0, 2)], np.int32)
+    return probs, tables, tiles
+
+
+@pytest.mark.parametrize("combine", [O.COMBINE_MEAN, O.COMBINE_WORST])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tile_dbs_end_state_is_tile_locally_optimal(tiny_two_freq, combine, seed):
+    probs, tables, tiles = tiny_two_freq
+    kind = probs[0].obj_kind
+    comb = np.array([O.combined_objective([t[m] for t in tables], kind, combine) for m in range(2 ** 12)])
+    b0 = W.random_design(12, seed)
+    order = np.tile(np.arange(len(tiles), dtype=np.int32), (30, 1))
+    res = O.dbs_tiles(probs, b0, tiles, order, tau=1e-9, combine=combine)
+    assert res.sweeps_done < 30
+    assert res.f == comb[_code(res.b)]
+    for tile in tiles:
+        nb = O.flip_tile(res.b, tile)
+        assert comb[_code(nb)] - res.f <= 1e-9 * abs(res.f)
+    b, f = b0.copy(), comb[_code(b0)]
+    for (_, _, ti, f_after) in res.accepted:
+        b = O.flip_tile(b, tiles[ti])
+        assert f_after == comb[_code(b)] and f_after > f + 1e-9 * abs(f)
+        f = f_after
+    # BEST takes the enumerated best tile neighbour every step
+    best = O.dbs_tiles(probs, b0, tiles, order, tau=1e-9, mode=O.BEST_IMPROVEMENT, combine=combine)
+    b = b0.copy()
+    for (_, _, ti, f_after) in best.accepted:
+        nbr = [comb[_code(O.flip_tile(b, t))] for t in tiles]
+        assert ti == int(np.argmax(nbr))
+        b = O.flip_tile(b, tiles[ti])
+        assert f_after == comb[_code(b)]
+
+
+def test_planted_tile_mistakes_are_caught(tiny_two_freq, monkeypatch):
+    """Flipping only a tile's first pixel, or combining by the wrong rule, breaks
+    the enumerated end-state pin."""
+    probs, tables, tiles = tiny_two_freq
+    kind = probs[0].obj_kind
+    worst = np.array([O.combined_objective([t[m] for t in tables], kind, O.COMBINE_WORST) for m in range(2 ** 12)])
+    order = np.tile(np.arange(len(tiles), dtype=np.int32), (30, 1))
+    b0 = W.random_design(12, 1)
+    real_flip = O.pngf_oracle.flip_tile
+    monkeypatch.setattr(O.pngf_oracle, "flip_tile", lambda b, tile: real_flip(b, tile[:1]))
+    res = O.dbs_tiles(probs, b0, tiles, order, tau=1e-9, combine=O.COMBINE_WORST)
+    monkeypatch.undo()
+    ok = all(worst[_code(real_flip(res.b, t))] - res.f <= 1e-9 * abs(res.f) for t in tiles)
+    assert not (ok and res.f == worst[_code(res.b)]), "first pixel only"
+    monkeypatch.setattr(O.pngf_oracle, "combined_objective", lambda fs, k, c: float(np.mean(fs)))
+    res = O.dbs_tiles(probs, b0, tiles, order, tau=1e-9, combine=O.COMBINE_WORST)
+    monkeypatch.undo()
+    assert res.f != worst[_code(res.b)], "mean instead of min-max"
