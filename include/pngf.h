@@ -229,6 +229,68 @@ pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n
                                  double* const* trace_f, int32_t trace_cap, int64_t* counters,
                                  void* batch_ws, size_t batch_ws_bytes);
 
+/*
+ * Tile flips on one or several systems (FP64).
+ *
+ * A candidate flips every pixel of one tile at once: the paper's tile flips of
+ * M unknowns (section "Low-rank update evaluation": dP_n = Q^T H_P Q, scored
+ * by Eq. 14 and kept by the rank-M Woodbury update of Eq. 9; its designs flip
+ * 2 to 4 symmetry-tied tiles together, Methods, "Optimization parameters").
+ * In field form, for tile K of m pixels with contrast changes D:
+ *   A = I - D W_KK (m x m), score o + T[:, K] A^-1 D e_K,
+ *   keep W += U Z U^T with U = W[:, K], Z = A^-1 D (and e, T, diag W, b, v).
+ * Several systems -- one per frequency: the paper precomputes G, G_obj and
+ * C^-1 per frequency and updates them independently ("Computational
+ * efficiency") -- share the design; every candidate is scored in every system
+ * and the objectives are combined into one (Supplementary Note 9: a mean or a
+ * min-max rule), which decides with the first system's tau.
+ *
+ *   ctxs     host array of n_sys contexts (1..PNGF_TILES_MAX_SYSTEMS), all FP64,
+ *            factored at the same design, same n_d, objective kind and mode and
+ *            device; the launch goes to ctxs[0]'s stream, which must order
+ *            every context's earlier work; refresh_k and n_ctas of ctxs[0] apply;
+ *            device-side errors are latched in ctxs[0]
+ *   combine  pngf_combine
+ *   tiles    int32 n_tiles x tile_m (device): the distinct pixels of each tile,
+ *            -1 entries pad (1 <= tile_m <= PNGF_TILE_MAX); an entry outside
+ *            [-1, n_d) latches PNGF_EINVAL
+ *   ws       device scratch of pngf_tiles_workspace_size bytes, 256-byte aligned
+ * A candidate whose m x m system meets a pivot below 1e-14 in magnitude (in
+ * any system) is skipped, as |d_k| < 1e-14 is for single pixels.
+ */
+#define PNGF_TILES_MAX_SYSTEMS 4
+#define PNGF_TILE_MAX 16
+typedef enum {
+  PNGF_COMBINE_MEAN = 0, /* arithmetic mean of the systems' objectives */
+  PNGF_COMBINE_WORST = 1 /* the worst system: min of maximised, max of minimised objectives */
+} pngf_combine;
+
+pngf_status pngf_tiles_workspace_size(int32_t n_sys, int32_t n_d, int32_t n_tiles, int32_t tile_m,
+                                      size_t* bytes);
+
+/* DBS over tiles with pngf_dbs_sweep's semantics, tiles in place of pixels:
+ * order int32 n_sweeps x n_tiles (device, rows permutations of the tile
+ * indices) or NULL (0..n_tiles-1); trace entries (sweep, position, tile, 0),
+ * trace_f the combined objective after each kept flip; counters as
+ * pngf_dbs_sweep's ([5] = 0).  Each context's own port amplitudes and
+ * objective are updated (pngf_eval_ports). */
+pngf_status pngf_dbs_sweep_tiles(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                                 int32_t n_tiles, int32_t tile_m, int32_t n_sweeps, const int32_t* order,
+                                 int32_t* trace, double* trace_f, int32_t trace_cap, int64_t* counters,
+                                 void* ws, size_t ws_bytes);
+
+/* Score listed tiles without changing the state: list int32 count (device,
+ * tile indices), F double count (device, out: combined objective, NaN if
+ * singular), f_sys double count x n_sys (device, out, or NULL). */
+pngf_status pngf_score_tiles(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                             int32_t n_tiles, int32_t tile_m, const int32_t* list, int32_t count, double* F,
+                             double* f_sys, void* ws, size_t ws_bytes);
+
+/* Keep the flip of one tile in every system (the rank-m update); a singular
+ * tile latches PNGF_ESINGULAR in ctxs[0] and changes nothing. */
+pngf_status pngf_accept_tile(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                             int32_t n_tiles, int32_t tile_m, int32_t tile, void* ws, size_t ws_bytes);
+
 /* Current port amplitudes x_obj (c128 n_o, host; Eq. 5, o = c_o + G_od (v .* e))
  * and objective of the S-parameters (host; the objective forms of
  * Supplementary Note 9); synchronizes. */

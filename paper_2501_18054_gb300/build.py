@@ -22,7 +22,8 @@ BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 LIBS = {
-    "libpngf.so": ["api.cu", "factor.cu", "sweep.cu", "sweep_mixed.cu", "batch.cu", "flush_tc.cu", "gradient.cu"],
+    "libpngf.so": ["api.cu", "factor.cu", "sweep.cu", "sweep_mixed.cu", "batch.cu", "flush_tc.cu", "gradient.cu",
+                   "general.cu"],
     "libpngf_peaks.so": ["peaks.cu"],
 }
 

@@ -333,6 +333,66 @@ pngf_status pngf_sync(pngf_ctx* c) {
   return (pngf_status)st;
 }
 
+pngf_status pngf_tiles_workspace_size(int32_t n_sys, int32_t n_d, int32_t n_tiles, int32_t tile_m, size_t* bytes) {
+  if (n_sys < 1 || n_sys > PNGF_TILES_MAX_SYSTEMS || n_d < 1 || n_d > 32768 || n_tiles < 1 ||
+      tile_m < 1 || tile_m > PNGF_TILE_MAX || !bytes)
+    return PNGF_EINVAL;
+  *bytes = tiles_workspace_bytes(n_sys, n_d, n_tiles, tile_m);
+  return PNGF_OK;
+}
+
+// the systems of one tile search: FP64, factored, one device, one size, objective and mode
+static pngf_status check_tile_call(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                                   int32_t n_tiles, int32_t tile_m, void* ws, size_t ws_bytes) {
+  if (!ctxs || n_sys < 1 || n_sys > PNGF_TILES_MAX_SYSTEMS || !tiles || n_tiles < 1 || tile_m < 1 ||
+      tile_m > PNGF_TILE_MAX || !ws)
+    return PNGF_EINVAL;
+  if (combine != PNGF_COMBINE_MEAN && combine != PNGF_COMBINE_WORST) return PNGF_EINVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return PNGF_EINVAL;
+  const pngf_ctx* c0 = ctxs[0];
+  if (!c0) return PNGF_EINVAL;
+  if (ws_bytes < tiles_workspace_bytes(n_sys, c0->cfg.n_d, n_tiles, tile_m)) return PNGF_ENOMEM;
+  for (int s = 0; s < n_sys; ++s) {
+    const pngf_ctx* c = ctxs[s];
+    if (!c) return PNGF_EINVAL;
+    if (!c->factored) return PNGF_ENOTFACTORED;
+    if (c->cfg.precision != PNGF_FP64 || c->cfg.n_d != c0->cfg.n_d || c->device != c0->device ||
+        c->cfg.objective != c0->cfg.objective || c->cfg.mode != c0->cfg.mode)
+      return PNGF_EINVAL;
+  }
+  return PNGF_OK;
+}
+
+pngf_status pngf_dbs_sweep_tiles(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                                 int32_t n_tiles, int32_t tile_m, int32_t n_sweeps, const int32_t* order,
+                                 int32_t* trace, double* trace_f, int32_t trace_cap, int64_t* counters, void* ws,
+                                 size_t ws_bytes) {
+  pngf_status st = check_tile_call(ctxs, n_sys, combine, tiles, n_tiles, tile_m, ws, ws_bytes);
+  if (st != PNGF_OK) return st;
+  if (n_sweeps < 0 || trace_cap < 0 || (trace_cap > 0 && !trace && !trace_f)) return PNGF_EINVAL;
+  if (n_sweeps == 0) return PNGF_OK;
+  return run_sweep_tiles(ctxs, n_sys, combine, tiles, n_tiles, tile_m, n_sweeps, order, -1, trace, trace_f,
+                         trace_cap, counters, ws);
+}
+
+pngf_status pngf_score_tiles(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                             int32_t n_tiles, int32_t tile_m, const int32_t* list, int32_t count, double* F,
+                             double* f_sys, void* ws, size_t ws_bytes) {
+  pngf_status st = check_tile_call(ctxs, n_sys, combine, tiles, n_tiles, tile_m, ws, ws_bytes);
+  if (st != PNGF_OK) return st;
+  if (count < 0 || (count > 0 && (!list || !F))) return PNGF_EINVAL;
+  return score_tiles(ctxs, n_sys, combine, tiles, n_tiles, tile_m, list, count, F, f_sys, ws);
+}
+
+pngf_status pngf_accept_tile(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combine, const int32_t* tiles,
+                             int32_t n_tiles, int32_t tile_m, int32_t tile, void* ws, size_t ws_bytes) {
+  pngf_status st = check_tile_call(ctxs, n_sys, combine, tiles, n_tiles, tile_m, ws, ws_bytes);
+  if (st != PNGF_OK) return st;
+  if (tile < 0 || tile >= n_tiles) return PNGF_EINVAL;
+  return run_sweep_tiles(ctxs, n_sys, combine, tiles, n_tiles, tile_m, 1, nullptr, tile, nullptr, nullptr, 0,
+                         nullptr, ws);
+}
+
 pngf_status pngf_gradient(pngf_ctx* c, double* grad, double* dodrho) {
   if (!c || !grad) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;

@@ -184,6 +184,13 @@ pngf_status set_wait_limit(pngf_ctx* c, unsigned long long polls, int hold_plus1
 pngf_status import_finish(pngf_ctx* c, int since_refresh);
 // gradient.cu
 pngf_status gradient(pngf_ctx* c, double* grad, double* dodrho);
+// general.cu
+size_t tiles_workspace_bytes(int n_sys, int n_d, int n_tiles, int tile_m);
+pngf_status run_sweep_tiles(pngf_ctx* const* ctxs, int n_sys, int combine, const int32_t* tiles, int n_tiles,
+                            int tile_m, int n_sweeps, const int32_t* order, int forced_tile, int32_t* trace,
+                            double* trace_f, int32_t trace_cap, int64_t* counters, void* ws);
+pngf_status score_tiles(pngf_ctx* const* ctxs, int n_sys, int combine, const int32_t* tiles, int n_tiles,
+                        int tile_m, const int32_t* list, int count, double* F, double* f_sys, void* ws);
 int sweep_grid_size(pngf_ctx* c);
 
 inline pngf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PNGF_OK : PNGF_ECUDA; }

@@ -28,6 +28,8 @@ PNGF_MAX_PORTS = 8
 PNGF_NOALLOC_MAX_ND = 8192
 PNGF_BATCH_MAX_RUNS = 65536
 PNGF_BATCH_MAX_ND = 4096
+PNGF_TILES_MAX_SYSTEMS, PNGF_TILE_MAX = 4, 16
+PNGF_COMBINE_MEAN, PNGF_COMBINE_WORST = 0, 1
 
 
 class pngf_config(ctypes.Structure):
@@ -84,6 +86,14 @@ def lib() -> ctypes.CDLL:
             "pngf_get_design": (st, [_P, _P]),
             "pngf_get_state": (st, [_P, _P, _P, _P, _P, _P]),
             "pngf_gradient": (st, [_P, _P, _P]),
+            "pngf_tiles_workspace_size": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+            "pngf_dbs_sweep_tiles": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_size_t]),
+            "pngf_score_tiles": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                      ctypes.c_int32, _P, _P, _P, ctypes.c_size_t]),
+            "pngf_accept_tile": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, _P, ctypes.c_size_t]),
             "pngf_get_since_refresh": (st, [_P, _P]),
             "pngf_set_state": (st, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
             "pngf_set_wait_limit": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
@@ -109,7 +119,8 @@ def exported_symbols() -> list:
     for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
               "pngf_accept_flip_noalloc", "pngf_batch_workspace_size", "pngf_dbs_sweep_batch",
               "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state",
-              "pngf_gradient", "pngf_get_since_refresh", "pngf_set_state", "pngf_set_wait_limit", "pngf_snapshot",
+              "pngf_gradient", "pngf_tiles_workspace_size", "pngf_dbs_sweep_tiles", "pngf_score_tiles",
+              "pngf_accept_tile", "pngf_get_since_refresh", "pngf_set_state", "pngf_set_wait_limit", "pngf_snapshot",
               "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
         if hasattr(L, n):
             names.append(n)
@@ -205,6 +216,41 @@ def pngf_get_state(ctx: int, W: Optional[int], diag_W: Optional[int], e: Optiona
 
 def pngf_gradient(ctx: int, grad: int, dodrho: Optional[int]) -> None:
     _check(lib().pngf_gradient(ctx, grad, dodrho), "pngf_gradient")
+
+
+def pngf_tiles_workspace_size(n_sys: int, n_d: int, n_tiles: int, tile_m: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().pngf_tiles_workspace_size(int(n_sys), int(n_d), int(n_tiles), int(tile_m), ctypes.byref(out)),
+           "pngf_tiles_workspace_size")
+    return int(out.value)
+
+
+def _ctx_array(ctxs):
+    h = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    return h, ctypes.cast(h, _P)
+
+
+def pngf_dbs_sweep_tiles(ctxs, combine: int, tiles: int, n_tiles: int, tile_m: int, n_sweeps: int,
+                         order: Optional[int], trace: Optional[int], trace_f: Optional[int], trace_cap: int,
+                         counters: Optional[int], ws: int, ws_bytes: int) -> None:
+    h, hp = _ctx_array(ctxs)
+    _check(lib().pngf_dbs_sweep_tiles(hp, len(ctxs), int(combine), tiles, int(n_tiles), int(tile_m), int(n_sweeps),
+                                      order, trace, trace_f, int(trace_cap), counters, ws, int(ws_bytes)),
+           "pngf_dbs_sweep_tiles")
+
+
+def pngf_score_tiles(ctxs, combine: int, tiles: int, n_tiles: int, tile_m: int, lst: int, count: int, F: int,
+                     f_sys: Optional[int], ws: int, ws_bytes: int) -> None:
+    h, hp = _ctx_array(ctxs)
+    _check(lib().pngf_score_tiles(hp, len(ctxs), int(combine), tiles, int(n_tiles), int(tile_m), lst, int(count), F,
+                                  f_sys, ws, int(ws_bytes)), "pngf_score_tiles")
+
+
+def pngf_accept_tile(ctxs, combine: int, tiles: int, n_tiles: int, tile_m: int, tile: int, ws: int,
+                     ws_bytes: int) -> None:
+    h, hp = _ctx_array(ctxs)
+    _check(lib().pngf_accept_tile(hp, len(ctxs), int(combine), tiles, int(n_tiles), int(tile_m), int(tile), ws,
+                                  int(ws_bytes)), "pngf_accept_tile")
 
 
 def pngf_get_since_refresh(ctx: int) -> int:
@@ -474,3 +520,70 @@ class DbsBatch:
             out.append(dict(trace=self.traces[i][:n_acc].cpu().numpy(), trace_f=self.trace_fs[i][:n_acc].cpu().numpy(),
                             counters=cnt[i]))
         return out
+
+
+class TileSearch:
+    """DBS over tile flips on one or several systems (one DbsContext each, FP64,
+    factored at the same design) that share the design: pngf_dbs_sweep_tiles."""
+
+    def __init__(self, contexts, tiles, combine: int = PNGF_COMBINE_MEAN):
+        import torch
+
+        self.torch = torch
+        self.ctxs = list(contexts)
+        c0 = self.ctxs[0]
+        self.device, self.stream = c0.device, c0.stream
+        t = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32))
+        if t.ndim == 1:
+            t = t[:, None]
+        self.n_tiles, self.tile_m = t.shape
+        self.tiles = torch.as_tensor(t).to(self.device)
+        self.combine = int(combine)
+        self.ws_bytes = pngf_tiles_workspace_size(len(self.ctxs), c0.n_d, self.n_tiles, self.tile_m)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.counters = torch.zeros(8, dtype=torch.int64, device=self.device)
+
+    def _h(self):
+        return [c.ctx for c in self.ctxs]
+
+    def dbs_sweep(self, n_sweeps: int, order=None, trace_cap: Optional[int] = None, sync: bool = True):
+        torch = self.torch
+        if trace_cap is None:
+            trace_cap = max(1, n_sweeps * self.n_tiles)
+        od = None
+        if order is not None:
+            od = torch.as_tensor(np.ascontiguousarray(order, dtype=np.int32)).to(self.device)
+        self._order_keep = od
+        self.trace = torch.zeros((trace_cap, 4), dtype=torch.int32, device=self.device)
+        self.trace_f = torch.zeros(trace_cap, dtype=torch.float64, device=self.device)
+        pngf_dbs_sweep_tiles(self._h(), self.combine, self.tiles.data_ptr(), self.n_tiles, self.tile_m, n_sweeps,
+                             od.data_ptr() if od is not None else None, self.trace.data_ptr(),
+                             self.trace_f.data_ptr(), trace_cap, self.counters.data_ptr(), self.ws.data_ptr(),
+                             self.ws_bytes)
+        if not sync:
+            return None
+        st = self.ctxs[0].sync()
+        if st != PNGF_OK:
+            raise PngfError(st, "pngf_dbs_sweep_tiles")
+        c = self.counters.cpu().numpy()
+        n_acc = int(min(c[0], trace_cap))
+        return dict(trace=self.trace[:n_acc].cpu().numpy(), trace_f=self.trace_f[:n_acc].cpu().numpy(), counters=c)
+
+    def score(self, tiles_idx=None, per_system: bool = False):
+        torch = self.torch
+        idx = np.arange(self.n_tiles, dtype=np.int32) if tiles_idx is None else np.asarray(tiles_idx, np.int32)
+        lst = torch.as_tensor(idx).to(self.device)
+        F = torch.empty(len(idx), dtype=torch.float64, device=self.device)
+        fs = torch.empty((len(idx), len(self.ctxs)), dtype=torch.float64, device=self.device) if per_system else None
+        pngf_score_tiles(self._h(), self.combine, self.tiles.data_ptr(), self.n_tiles, self.tile_m, lst.data_ptr(),
+                         len(idx), F.data_ptr(), fs.data_ptr() if fs is not None else None, self.ws.data_ptr(),
+                         self.ws_bytes)
+        self.stream.synchronize()
+        return (F.cpu().numpy(), fs.cpu().numpy()) if per_system else F.cpu().numpy()
+
+    def accept(self, tile: int) -> None:
+        pngf_accept_tile(self._h(), self.combine, self.tiles.data_ptr(), self.n_tiles, self.tile_m, int(tile),
+                         self.ws.data_ptr(), self.ws_bytes)
+        st = self.ctxs[0].sync()
+        if st != PNGF_OK:
+            raise PngfError(st, "pngf_accept_tile")
