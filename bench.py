@@ -33,8 +33,8 @@ METRIC = "DBS pixel-flip evals/sec at N_d=4096, mixed vs FP64 at 1e-4 S-param er
 UNIT = "evals/s"
 WORKLOAD = "fdfd256_nd4096"  # 256^2 FDFD, 16-cell PML, eps=2.2 slab, 64x64 design {1,10}, 2 ports
 
-# DRAM traffic of the search kernel from one ncu capture (profiles/dbs_mixed_kernel_fdfd256_nd4096.md:
-# one launch = one full run, seed 0): measured read + write bytes over the algorithmic bytes of
+# DRAM traffic of the search kernel from one ncu capture of that kernel on this workload
+# (one launch = one full run, seed 0): measured read + write bytes over the algorithmic bytes of
 # that launch.  A step's traffic is this ratio times the step's algorithmic bytes, reported only
 # while the kernel code is the captured one (fingerprint of the sources without comments), else null.
 TRAFFIC_CAPTURE = {"kernel": "dbs_mixed_kernel", "workload": "fdfd256_nd4096",
@@ -105,6 +105,8 @@ def parse():
     ap.add_argument("--cpu-sample-evals", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="mixed path: choose runs per GPU, delay R and fold engine from timed trials first")
     return ap.parse_args()
 
 
@@ -362,7 +364,8 @@ def bench_batch(args, torch, dist, dev, P, Wl):
                     config={"workload": BATCH_WORKLOAD, "runs": len(runs), "n_d": "256/576/1024 (b mod 3)",
                             "precision": "fp64", "mode": "first-improvement, raster order",
                             "max_sweeps": args.sweeps, "refresh_k": args.refresh_k, "tau": args.tau,
-                            "step": "restore every run's factored start + one batched launch to convergence",
+                            "step": "restore every run's factored start + one batched launch, up to %d sweeps "
+                                    "or until a sweep keeps no flip" % args.sweeps,
                             "l2": "inputs larger than L2 (W of all runs ~%.1f GB)" % (
                                 sum(c.n_d ** 2 for c, _ in runs) * 16 / 1e9)},
                     roofline=roofline, cpu_baseline=None, e2e=None, clocks=clk, gpu_launches=args.steps,
@@ -418,12 +421,14 @@ class RunSet:
         self.inputs = inputs
         self.kev = None
 
-    def step(self, i_step=None, orders=None):
+    def step(self, i_step=None, orders=None, subset=None):
         torch, P = self.torch, self.P
         fork = torch.cuda.Event()
         fork.record(self.tstream)
         joins = []
         for r, (c, s) in enumerate(zip(self.ctxs, self.streams)):
+            if subset is not None and r not in subset:
+                continue
             s.wait_event(fork)
             P.pngf_restore(c.ctx)
             if i_step is not None:
@@ -453,6 +458,60 @@ class RunSet:
             c.close()
 
 
+def autotune_launch(args, torch, P, Wl, case, dev, nsm, tstream):
+    """Choose runs per GPU, the delay R and the fold engine of the mixed search
+    from timed trials (paper_2501_18054_gb300.autotune): every trial's final
+    designs must equal the FP64 path's from the same starts, with S within 1e-4."""
+    import argparse
+    from paper_2501_18054_gb300 import autotune as A
+    cands = A.candidates(case.n_d, nsm, args.refresh_k, runs_options=(1, 2, 4), delay_options=(32, 64))
+    max_runs = max(c.runs for c in cands)
+    seeds = list(range(max_runs))
+    ref = RunSet(torch, P, Wl, case, dev, P.PNGF_FP64, args, seeds, nsm // max_runs, tstream)
+    ref.step()
+    torch.cuda.synchronize(dev)
+    if any(st != 0 for st in ref.status()):
+        raise RuntimeError("autotune: FP64 reference runs failed")
+    ref_out = [(cx.design(), (cx.eval_ports()[0] - case.s_off) * case.s_scale) for cx in ref.ctxs]
+    inputs = ref.inputs
+    ref.close()
+    sets = {}
+    for r in sorted({c.delay_r for c in cands}):
+        a2 = argparse.Namespace(**vars(args))
+        a2.delay_r = r
+        sets[r] = RunSet(torch, P, Wl, case, dev, P.PNGF_MIXED, a2, seeds, nsm // max_runs, tstream, inputs=inputs)
+
+    def measure(cand, steps):
+        rs = sets[cand.delay_r]
+        sub = set(range(cand.runs))
+        for i in sub:
+            rs.ctxs[i].set_launch(cand.ctas, cand.tensor_fold)
+        rs.step(subset=sub)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(tstream)
+        for _ in range(steps):
+            rs.step(subset=sub)
+        t1.record(tstream)
+        torch.cuda.synchronize(dev)
+        ok = all(rs.ctxs[i].sync() == 0 for i in sub)
+        cnt = rs.counts()
+        evals = float(sum(cnt[i, 1] for i in sub)) * steps
+        same, err = True, 0.0
+        for i in sub:
+            b = rs.ctxs[i].design()
+            same = same and bool(np.array_equal(b, ref_out[i][0]))
+            if same:
+                S = (rs.ctxs[i].eval_ports()[0] - case.s_off) * case.s_scale
+                S_ref = ref_out[i][1]
+                err = max(err, float(np.max(np.abs(S - S_ref) / np.maximum(np.abs(S_ref), 1e-3))))
+        return A.Trial(cand, steps, evals / (t0.elapsed_time(t1) / 1e3), err, same, ok)
+
+    win, trials = A.tune(cands, measure)
+    for rs in sets.values():
+        rs.close()
+    return win, trials
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -477,10 +536,18 @@ def main():
     n, n_o = case.n_d, case.n_o
     prec = P.PNGF_MIXED if args.precision == "mixed" else P.PNGF_FP64
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    tstream = torch.cuda.Stream(dev)
+    tuned = None
+    if prec == P.PNGF_MIXED and args.autotune:
+        win, trials = autotune_launch(args, torch, P, Wl, case, dev, nsm, tstream)
+        args.runs, args.delay_r, args.tensor_fold = win.cand.runs, win.cand.delay_r, win.cand.tensor_fold
+        tuned = {"chosen": win.cand.as_dict(), "chosen_evals_per_s": win.evals_per_s, "bar": 1e-4,
+                 "trials": [t.as_dict() for t in trials],
+                 "note": "successive halving over runs per GPU x delay R x fold engine; every trial's final "
+                         "designs equal the FP64 path's and S within 1e-4"}
     n_runs = max(1, args.runs)
     ctas = 0 if n_runs == 1 else nsm // n_runs
     seeds = [dist.rank * n_runs + i for i in range(n_runs)]
-    tstream = torch.cuda.Stream(dev)
     rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream)
     for _ in range(max(args.warmup, 1)):
         rs.step()
@@ -684,7 +751,8 @@ def main():
                     "delay_r": args.delay_r if prec == P.PNGF_MIXED else None,
                     "fold": ("tcgen05 3xTF32" if args.tensor_fold else "FP32 CUDA cores")
                     if prec == P.PNGF_MIXED else None,
-                    "step": "restore every run's factored start state + DBS to convergence, runs concurrent",
+                    "step": "restore every run's factored start state + DBS for up to %d sweeps or until "
+                            "a sweep keeps no flip, runs concurrent" % args.sweeps,
                     "l2": "inputs larger than L2 (W = %.0f MB complex128 per run)" % (n * n * 16 / 1e6),
                     "replicas": "independent runs per GPU (seed = rank * runs + i)"},
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk, gpu_launches=args.steps * n_runs,
@@ -692,7 +760,7 @@ def main():
             accepts_per_s=acc_per_step * args.steps / (ms_max / 1e3),
             sweeps_per_s=sweeps_per_step * args.steps / (ms_max / 1e3),
             kernel_ms_avg=k_avg, factor_ms=statistics.mean(rs.factor_ms), fp64_peak_gflops=peak_fp64,
-            phase_ms_cta0=phase_ms, mixed_vs_fp64=compare)
+            phase_ms_cta0=phase_ms, mixed_vs_fp64=compare, autotune=tuned)
         print(json.dumps(line))
     rs.close()
     return 0

@@ -380,6 +380,16 @@ pngf_status pngf_restore(pngf_ctx* ctx);
  */
 pngf_status pngf_get_phase_cycles(pngf_ctx* ctx, int64_t* host16);
 
+/*
+ * Launch settings of later searches on this context (no counterpart in the
+ * paper; what an autotuner varies between timed trials without re-factoring):
+ *   n_ctas       persistent grid of pngf_dbs_sweep (0 = one per SM, as at create)
+ *   tensor_fold  PNGF_MIXED: 1 = fold the delayed set on the tensor cores,
+ *                0 = on the FP32 CUDA cores; must be 0 for FP64 contexts
+ * The search state is untouched; call between searches, on the context's stream.
+ */
+pngf_status pngf_set_launch(pngf_ctx* ctx, int32_t n_ctas, int32_t tensor_fold);
+
 /* Synchronize the stream and return the latched device status (then clear it). */
 pngf_status pngf_sync(pngf_ctx* ctx);
 

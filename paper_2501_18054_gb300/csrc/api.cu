@@ -393,6 +393,15 @@ pngf_status pngf_accept_tile(pngf_ctx* const* ctxs, int32_t n_sys, int32_t combi
                          nullptr, ws);
 }
 
+pngf_status pngf_set_launch(pngf_ctx* c, int32_t n_ctas, int32_t tensor_fold) {
+  if (!c || n_ctas < 0 || (tensor_fold != 0 && tensor_fold != 1)) return PNGF_EINVAL;
+  if (tensor_fold && c->cfg.precision != PNGF_MIXED) return PNGF_EINVAL;
+  c->cfg.n_ctas = n_ctas;
+  c->cfg.tensor_fold = tensor_fold;
+  c->coop_ctas = sweep_grid_size(c);
+  return PNGF_OK;
+}
+
 pngf_status pngf_gradient(pngf_ctx* c, double* grad, double* dodrho) {
   if (!c || !grad) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;

@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "pngf_get_design": (st, [_P, _P]),
             "pngf_get_state": (st, [_P, _P, _P, _P, _P, _P]),
             "pngf_gradient": (st, [_P, _P, _P]),
+            "pngf_set_launch": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
             "pngf_tiles_workspace_size": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_size_t)]),
             "pngf_dbs_sweep_tiles": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
@@ -119,7 +120,7 @@ def exported_symbols() -> list:
     for n in ("pngf_workspace_size", "pngf_create", "pngf_factor", "pngf_score_flips", "pngf_accept_flip",
               "pngf_accept_flip_noalloc", "pngf_batch_workspace_size", "pngf_dbs_sweep_batch",
               "pngf_dbs_sweep", "pngf_eval_ports", "pngf_get_design", "pngf_get_state",
-              "pngf_gradient", "pngf_tiles_workspace_size", "pngf_dbs_sweep_tiles", "pngf_score_tiles",
+              "pngf_gradient", "pngf_set_launch", "pngf_tiles_workspace_size", "pngf_dbs_sweep_tiles", "pngf_score_tiles",
               "pngf_accept_tile", "pngf_get_since_refresh", "pngf_set_state", "pngf_set_wait_limit", "pngf_snapshot",
               "pngf_restore", "pngf_sync", "pngf_get_phase_cycles", "pngf_status_string", "pngf_destroy"):
         if hasattr(L, n):
@@ -251,6 +252,10 @@ def pngf_accept_tile(ctxs, combine: int, tiles: int, n_tiles: int, tile_m: int, 
     h, hp = _ctx_array(ctxs)
     _check(lib().pngf_accept_tile(hp, len(ctxs), int(combine), tiles, int(n_tiles), int(tile_m), int(tile), ws,
                                   int(ws_bytes)), "pngf_accept_tile")
+
+
+def pngf_set_launch(ctx: int, n_ctas: int, tensor_fold: int) -> None:
+    _check(lib().pngf_set_launch(ctx, int(n_ctas), int(tensor_fold)), "pngf_set_launch")
 
 
 def pngf_get_since_refresh(ctx: int) -> int:
@@ -450,6 +455,10 @@ class DbsContext:
                        keep["d"].data_ptr(), keep["e"].data_ptr(), keep["T"].data_ptr(), keep["o"].data_ptr(),
                        int(ck["since_refresh"]))
         self.stream.synchronize()
+
+    def set_launch(self, n_ctas: int, tensor_fold: int) -> None:
+        pngf_set_launch(self.ctx, n_ctas, tensor_fold)
+        self.cfg.n_ctas, self.cfg.tensor_fold = int(n_ctas), int(tensor_fold)
 
     def set_wait_limit(self, wait_log2: int, hold_cta: int = -1) -> None:
         pngf_set_wait_limit(self.ctx, wait_log2, hold_cta)
