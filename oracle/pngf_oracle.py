@@ -23,6 +23,9 @@ binary design ``b``):
   design, visit tiles one at a time, flip, evaluate, keep the flip if the
   objective improved, otherwise undo it; stop when a whole pass over the tiles
   brings no improvement.  Every visited flip is re-solved from scratch.
+* ``evaluate_pec``: the objective of a design of perfect-conductor pixels
+  from the paper's own PEC system, Eq. 2: [(I - P) + P G] j = P e_inc (with
+  this code's sign of G); ``dbs(..., evaluator=evaluate_pec)`` searches it.
 * ``dbs_tiles``: DBS whose candidates flip a whole tile (several pixels at
   once, the paper's rank-M flips) on one or several systems that share the
   design (the paper's per-frequency systems), the per-system objectives
@@ -139,18 +142,40 @@ def evaluate(p: Problem, b: np.ndarray) -> Evaluation:
     return Evaluation(e, o, S, objective(S, p.obj_kind, p.obj_weights))
 
 
-def candidate_objectives(p: Problem, b: np.ndarray, pixels) -> np.ndarray:
+def pec_system(G: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """C = (I - P) - P G: Eq. 2 of the paper, [(I - P) + P G] j = P e_inc, written
+    with this code's sign of G (the total field is c_d + G j, the paper's is
+    e_inc - G j), for a design of perfect electric conductor (PEC) pixels
+    (P = diag(b), 1 = metal): on a metal pixel the total field vanishes, on an
+    empty pixel the current does."""
+    n = G.shape[0]
+    P = np.diag(np.asarray(b, dtype=np.float64))
+    return np.eye(n, dtype=np.complex128) - P - P @ G
+
+
+def evaluate_pec(p: Problem, b: np.ndarray) -> Evaluation:
+    """Objective of a PEC design from scratch: C j = P c_d (Eq. 2), o = c_o + G_od j
+    (Eq. 5); ``e`` is the total field c_d + G j (zero on metal)."""
+    b = np.asarray(b, dtype=np.uint8)
+    j = sla.solve(pec_system(p.G, b), b * p.c_d, check_finite=True)
+    o = p.c_o + p.G_od @ j
+    S = s_params(o, p.s_off, p.s_scale)
+    return Evaluation(p.c_d + p.G @ j, o, S, objective(S, p.obj_kind, p.obj_weights))
+
+
+def candidate_objectives(p: Problem, b: np.ndarray, pixels, evaluator=None) -> np.ndarray:
     """Objective after flipping each listed pixel alone (re-solved from scratch).
 
-    A singular candidate gets NaN.
+    A singular candidate gets NaN.  ``evaluator``: evaluate (default) or evaluate_pec.
     """
+    ev_fn = evaluate if evaluator is None else evaluator
     out = np.empty(len(pixels), dtype=np.float64)
     b = np.asarray(b, dtype=np.uint8)
     for i, k in enumerate(pixels):
         b2 = b.copy()
         b2[k] ^= 1
         try:
-            out[i] = evaluate(p, b2).f
+            out[i] = ev_fn(p, b2).f
         except np.linalg.LinAlgError:
             out[i] = np.nan
     return out
@@ -227,7 +252,7 @@ class DbsResult:
 
 def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
         mode: int = FIRST_IMPROVEMENT, max_evals: Optional[int] = None,
-        keep_margins: bool = False) -> DbsResult:
+        keep_margins: bool = False, evaluator=None) -> DbsResult:
     """Direct binary search, every candidate re-solved from scratch.
 
     ``order`` has shape (n_sweeps, n_d): the visiting order of each sweep.
@@ -235,10 +260,12 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
     BEST: at each step flip the best improving pixel of the whole region
     (ties -> lowest pixel index) and count one sweep per step.
     A sweep without any accepted flip ends the search (converged).
-    ``max_evals`` bounds the work (used for timing samples).
+    ``max_evals`` bounds the work (used for timing samples).  ``evaluator``:
+    evaluate (default, the general-material field form) or evaluate_pec.
     """
+    evaluate_ = evaluate if evaluator is None else evaluator
     b = np.asarray(b0, dtype=np.uint8).copy()
-    cur = evaluate(p, b)
+    cur = evaluate_(p, b)
     f = cur.f
     accepted: List[tuple] = []
     n_evals = 0
@@ -256,7 +283,7 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
                 b2[k] ^= 1
                 n_evals += 1
                 try:
-                    ev = evaluate(p, b2)
+                    ev = evaluate_(p, b2)
                 except np.linalg.LinAlgError:
                     continue
                 margin = improvement(ev.f, f, p.obj_kind) - tau * max(abs(f), 1e-30)
@@ -269,7 +296,7 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
                     any_accept = True
         else:
             cand = np.arange(p.n_d)
-            fs = candidate_objectives(p, b, cand)
+            fs = candidate_objectives(p, b, cand, evaluator)
             n_evals += p.n_d
             gains = np.array([improvement(x, f, p.obj_kind) if np.isfinite(x) else -np.inf for x in fs])
             m = gains - tau * max(abs(f), 1e-30)
@@ -278,7 +305,7 @@ def dbs(p: Problem, b0: np.ndarray, order: np.ndarray, tau: float = 1e-9,
             if m[best] > 0:
                 b = b.copy()
                 b[best] ^= 1
-                cur = evaluate(p, b)
+                cur = evaluate_(p, b)
                 f = cur.f
                 accepted.append((s, 0, best, f))
                 any_accept = True

@@ -406,3 +406,76 @@ def test_planted_tile_mistakes_are_caught(tiny_two_freq, monkeypatch):
     res = O.dbs_tiles(probs, b0, tiles, order, tau=1e-9, combine=O.COMBINE_WORST)
     monkeypatch.undo()
     assert res.f != worst[_code(res.b)], "mean instead of min-max"
+
+
+# ---------------------------------------------------------------- perfect-conductor (PEC) pixels, Eq. 2
+def _full_structure_pec(case, b):
+    """Port amplitudes of the full FDFD structure with every metal design node
+    held at E = 0 (a perfect conductor), by a direct sparse solve without them."""
+    import scipy.sparse.linalg as spl
+    spec = W.SPECS[case.name]
+    eps = W._eps_grid(spec)
+    A, sxy = W.helmholtz_operator(eps, spec.npml, W._k(spec), npml_y=spec.npml_y)
+    s, Pi = W._source_and_ports(spec, W._eps_grid(spec))
+    metal = W._design_nodes(spec)[np.asarray(b, bool)]
+    keep = np.setdiff1d(np.arange(A.shape[0]), metal)
+    A = A.tocsr()
+    E = np.zeros(A.shape[0], complex)
+    E[keep] = spl.splu(A[keep][:, keep].tocsc()).solve(-(sxy * s)[keep])
+    return E[W._design_nodes(spec)], Pi @ E
+
+
+@pytest.mark.parametrize("name,seed", [("fdfd64", 3), ("fdfd128_metal", 2)])
+def test_pec_system_equals_full_fdfd_with_conductors(name, seed, fdfd64, metal128):
+    case = fdfd64 if name == "fdfd64" else metal128
+    b = W.random_design(case.n_d, seed)
+    ev = O.evaluate_pec(O.Problem.from_case(case), b)
+    e_full, o_full = _full_structure_pec(case, b)
+    assert np.max(np.abs(ev.o - o_full)) <= 1e-10 * np.max(np.abs(o_full))
+    assert np.max(np.abs(ev.e - e_full)) <= 1e-10 * np.max(np.abs(e_full))
+    assert np.max(np.abs(ev.e[b == 1])) <= 1e-12 * np.max(np.abs(e_full))  # no field inside the conductor
+
+
+def test_pec_is_the_limit_of_lossy_metal(metal128):
+    """The general-material system with eps_on = 1 + i s tends to the PEC system
+    as s grows, the difference falling like 1/s."""
+    p = O.Problem.from_case(metal128)
+    b = W.random_design(metal128.n_d, 4)
+    o_pec = O.evaluate_pec(p, b).o
+    k2 = metal128.dv[0] / 1e4j  # k^2 of the workload (dv = k^2 * 1e4 i)
+    errs = []
+    for sig in (1e5, 1e7, 1e9):
+        p.dv = np.full(metal128.n_d, k2 * sig * 1j)
+        errs.append(np.max(np.abs(O.evaluate(p, b).o - o_pec)) / np.max(np.abs(o_pec)))
+    assert errs[2] < 1e-6
+    assert errs[1] < 3e-2 * errs[0] and errs[2] < 3e-2 * errs[1]
+
+
+def test_pec_dbs_end_state_is_locally_optimal(fdfd64):
+    s = _tiny(fdfd64)
+    p = O.Problem.from_case(s)
+    fs = np.array([O.evaluate_pec(p, np.array([(m >> i) & 1 for i in range(12)], np.uint8)).f
+                   for m in range(2 ** 12)])
+    for seed in (0, 1):
+        res = O.dbs(p, W.random_design(12, seed), W.raster_order(12, 60), tau=1e-9, evaluator=O.evaluate_pec)
+        assert res.sweeps_done < 60 and res.f == fs[_code(res.b)]
+        for k in range(12):
+            nb = res.b.copy(); nb[k] ^= 1
+            assert fs[_code(nb)] - res.f <= 1e-9 * abs(res.f)
+
+
+def test_planted_pec_mistakes_are_caught(metal128, monkeypatch):
+    b = W.random_design(metal128.n_d, 2)
+    _, o_full = _full_structure_pec(metal128, b)
+    p = O.Problem.from_case(metal128)
+    n = metal128.n_d
+    plants = {
+        "the paper's sign of G kept": lambda G, bb: np.eye(n) - np.diag(bb * 1.0) + np.diag(bb * 1.0) @ G,
+        "(I - P) dropped": lambda G, bb: 1e-3 * np.eye(n) - np.diag(bb * 1.0) @ G,
+        "G P instead of P G": lambda G, bb: np.eye(n) - np.diag(bb * 1.0) - G @ np.diag(bb * 1.0),
+    }
+    for what, bad in plants.items():
+        monkeypatch.setattr(O.pngf_oracle, "pec_system", bad)
+        o = O.evaluate_pec(p, b).o
+        assert np.max(np.abs(o - o_full)) > 1e-6 * np.max(np.abs(o_full)), what
+    monkeypatch.undo()
