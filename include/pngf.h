@@ -73,8 +73,17 @@ typedef enum {
 /* PNGF_FP64: every step in FP64.  PNGF_MIXED: an FP32 maintained inverse with a
  * delayed rank-delay_r correction, the decision state (diag W, e, T, o, f) as
  * FP32 pairs (~48 bits, FP32 exponent range: magnitudes and their squares must
- * stay within about 1e+-38), refreshed against G every refresh_k flips. */
-typedef enum { PNGF_FP64 = 0, PNGF_MIXED = 1 } pngf_precision;
+ * stay within about 1e+-38), refreshed against G every refresh_k flips.
+ * PNGF_PEC: FP64, pixels of perfect electric conductor (the paper's binary
+ * system, Eq. 2, [(I - P) + P G] j = P e_inc; dv is not used): the search
+ * keeps H = (G_MM)^-1 of the metal set M, Q = G H and W = G - G H G, and a
+ * flip is a symmetric rank-1 change of H and W and a rank-1 change of Q; the
+ * state of a design is built from the empty design by rank-1 additions
+ * (pngf_factor).  No refresh (refresh_k is ignored); pngf_set_state,
+ * pngf_gradient, pngf_score_flips' o_new, the batch and tile calls are not
+ * available (PNGF_EINVAL).  pngf_get_state returns W (upper triangle current),
+ * diag W, the total field e (zero on metal) and T = G_od - G_od H G. */
+typedef enum { PNGF_FP64 = 0, PNGF_MIXED = 1, PNGF_PEC = 2 } pngf_precision;
 typedef enum { PNGF_FIRST_IMPROVEMENT = 0, PNGF_BEST_IMPROVEMENT = 1 } pngf_dbs_mode;
 typedef enum {
   PNGF_OBJ_MAX_WEIGHTED_POWER = 0, /* maximise sum_p w_p |S_p|^2 */

@@ -149,8 +149,8 @@ def pec_system(G: np.ndarray, b: np.ndarray) -> np.ndarray:
     (P = diag(b), 1 = metal): on a metal pixel the total field vanishes, on an
     empty pixel the current does."""
     n = G.shape[0]
-    P = np.diag(np.asarray(b, dtype=np.float64))
-    return np.eye(n, dtype=np.complex128) - P - P @ G
+    p = np.asarray(b, dtype=np.float64)
+    return np.eye(n, dtype=np.complex128) - np.diag(p) - p[:, None] * G  # P G: rows of G scaled by P
 
 
 def evaluate_pec(p: Problem, b: np.ndarray) -> Evaluation:
@@ -160,7 +160,9 @@ def evaluate_pec(p: Problem, b: np.ndarray) -> Evaluation:
     j = sla.solve(pec_system(p.G, b), b * p.c_d, check_finite=True)
     o = p.c_o + p.G_od @ j
     S = s_params(o, p.s_off, p.s_scale)
-    return Evaluation(p.c_d + p.G @ j, o, S, objective(S, p.obj_kind, p.obj_weights))
+    # e = c_d + G j, summed by numpy itself (a threaded BLAS matrix-vector
+    # product of this size spends far longer starting threads than computing)
+    return Evaluation(p.c_d + np.einsum("ij,j->i", p.G, j), o, S, objective(S, p.obj_kind, p.obj_weights))
 
 
 def candidate_objectives(p: Problem, b: np.ndarray, pixels, evaluator=None) -> np.ndarray:

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 LIBS = {
     "libpngf.so": ["api.cu", "factor.cu", "sweep.cu", "sweep_mixed.cu", "batch.cu", "flush_tc.cu", "gradient.cu",
-                   "general.cu"],
+                   "general.cu", "pec.cu"],
     "libpngf_peaks.so": ["peaks.cu"],
 }
 

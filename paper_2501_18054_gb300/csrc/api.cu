@@ -16,6 +16,7 @@ Layout make_layout(const pngf_config& cfg) {
   Layout L{};
   const size_t n = (size_t)cfg.n_d, n_o = (size_t)cfg.n_o;
   const bool mixed = cfg.precision == PNGF_MIXED;
+  const bool pec = cfg.precision == PNGF_PEC;
   L.ldw = (int)align_up(n + 1, 8);
   L.ldl = (int)align_up(n, 32);
   L.ldt = (int)align_up(n, 8);
@@ -29,14 +30,15 @@ Layout make_layout(const pngf_config& cfg) {
   };
   const size_t c = sizeof(c128);
   L.W = take(n * L.ldw * c);
-  L.LU = take(n * L.ldw * c);
+  L.LU = take(n * L.ldw * c);  // PEC: H = (G_MM)^-1 padded
+  L.Q = take(pec ? n * L.ldw * c : 0);  // PEC: Q = G H (full)
   // mixed path: [Wlo_re | Wlo_im | X | xa] contiguous, so one copy snapshots them
   const size_t plane = n * L.ldl * sizeof(float);
   L.Wlo_re = take(mixed ? 2 * plane : 0);
   L.Wlo_im = L.Wlo_re + (mixed ? plane : 0);
   L.X = take(n * (size_t)L.R * 2 * sizeof(float));
   L.xa = take((size_t)L.R * c);
-  L.snapW_bytes = mixed ? off - L.Wlo_re : n * L.ldw * c;
+  L.snapW_bytes = mixed ? off - L.Wlo_re : pec ? off - L.W : n * L.ldw * c;  // PEC: W, H, Q contiguous
   // contiguous state block: diag, e, T, v, b
   L.diag = off;
   off += align_up(n * c, 256);
@@ -48,6 +50,14 @@ Layout make_layout(const pngf_config& cfg) {
   off += align_up(n * c, 256);
   L.b = off;
   off += align_up(n, 256);
+  if (pec) {  // PEC: current j, R = G_od H, diag H
+    L.pj = off;
+    off += align_up(n * c, 256);
+    L.pR = off;
+    off += align_up(n_o * L.ldt * c, 256);
+    L.pdiagH = off;
+    off += align_up(n * c, 256);
+  }
   L.state_bytes = off - L.diag;
   L.pos_of = take(n * sizeof(int));
   L.part = take((size_t)L.n_part * (2 * sizeof(long long) + 2 * sizeof(double) + kMaxPorts * c));
@@ -62,7 +72,7 @@ Layout make_layout(const pngf_config& cfg) {
   L.cbuf = take(n * c);
   L.rbuf = take(4 * (1 + n_o) * n * c + 1024);
   L.actg = take(n * sizeof(int));  // active-pixel list of the refresh
-  L.gsum = take(n * n * sizeof(double));  // Re G + Im G (three-multiplication refresh products)
+  L.gsum = take(pec ? 0 : n * n * sizeof(double));  // Re G + Im G (three-multiplication refresh products)
   // mixed path: G as FP32 pairs (double-float refresh residual) and the split refined vectors
   L.gsplit = take(mixed ? n * n * 4 * sizeof(float) : 0);
   L.xs = take(mixed ? (1 + n_o) * n * 8 * sizeof(float) : 0);
@@ -79,7 +89,7 @@ static pngf_status check_config(const pngf_config* cfg) {
   if (!cfg) return PNGF_EINVAL;
   if (cfg->n_d < 1 || cfg->n_d > 32768) return PNGF_EINVAL;
   if (cfg->n_o < 1 || cfg->n_o > PNGF_MAX_PORTS) return PNGF_EINVAL;
-  if (cfg->precision != PNGF_FP64 && cfg->precision != PNGF_MIXED) return PNGF_EINVAL;
+  if (cfg->precision != PNGF_FP64 && cfg->precision != PNGF_MIXED && cfg->precision != PNGF_PEC) return PNGF_EINVAL;
   if (cfg->mode != PNGF_FIRST_IMPROVEMENT && cfg->mode != PNGF_BEST_IMPROVEMENT) return PNGF_EINVAL;
   if (cfg->objective != PNGF_OBJ_MAX_WEIGHTED_POWER && cfg->objective != PNGF_OBJ_MIN_INSERTION_LOSS)
     return PNGF_EINVAL;
@@ -163,6 +173,11 @@ pngf_status pngf_create(const pngf_config* cfg, const double* G_dd, const double
 
 pngf_status pngf_factor(pngf_ctx* c, const uint8_t* b) {
   if (!c || !b) return PNGF_EINVAL;
+  if (c->cfg.precision == PNGF_PEC) {
+    pngf_status st = factor_pec(c, b);
+    if (st == PNGF_OK) c->factored = true;
+    return st;
+  }
   pngf_status st = factor_fp64(c, b);
   if (st == PNGF_OK && c->cfg.precision == PNGF_MIXED) st = mixed_after_factor(c);
   if (st == PNGF_OK) c->factored = true;
@@ -172,12 +187,14 @@ pngf_status pngf_factor(pngf_ctx* c, const uint8_t* b) {
 pngf_status pngf_score_flips(pngf_ctx* c, const int32_t* pixels, int32_t n, double* f_new, double* o_new) {
   if (!c || n < 0 || (n > 0 && (!pixels || !f_new))) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
+  if (c->cfg.precision == PNGF_PEC) return o_new ? PNGF_EINVAL : score_flips_pec(c, pixels, n, f_new);
   return score_flips(c, pixels, n, f_new, o_new);
 }
 
 pngf_status pngf_accept_flip(pngf_ctx* c, int32_t pixel) {
   if (!c || pixel < 0 || pixel >= c->cfg.n_d) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
+  if (c->cfg.precision == PNGF_PEC) return accept_flip_pec(c, pixel);
   return c->cfg.precision == PNGF_MIXED ? accept_flip_mixed(c, pixel) : accept_flip(c, pixel);
 }
 
@@ -196,6 +213,7 @@ pngf_status pngf_dbs_sweep(pngf_ctx* c, int32_t n_sweeps, const int32_t* order, 
   if (!c->factored) return PNGF_ENOTFACTORED;
   if (n_sweeps == 0) return PNGF_OK;
   if (c->cfg.precision == PNGF_MIXED) return run_sweep_mixed(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
+  if (c->cfg.precision == PNGF_PEC) return run_sweep_pec(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
   return run_sweep(c, n_sweeps, order, trace, trace_f, trace_cap, counters);
 }
 
@@ -219,6 +237,7 @@ pngf_status pngf_dbs_sweep_batch(pngf_ctx* const* ctxs, int32_t n_ctx, int32_t n
     if (!c) return PNGF_EINVAL;
     if (!c->factored) return PNGF_ENOTFACTORED;
     if (c->cfg.precision != c0->cfg.precision || c->cfg.mode != c0->cfg.mode) return PNGF_EINVAL;
+    if (c->cfg.precision == PNGF_PEC) return PNGF_EINVAL;
     if (c->cfg.precision == PNGF_MIXED && c->cfg.tensor_fold != c0->cfg.tensor_fold) return PNGF_EINVAL;
     if (c->cfg.n_d > PNGF_BATCH_MAX_ND || c->device != c0->device) return PNGF_EINVAL;
   }
@@ -255,7 +274,7 @@ pngf_status pngf_get_state(pngf_ctx* c, double* W, double* diag_W, double* e, do
   const size_t n = c->cfg.n_d, n_o = c->cfg.n_o, cs = sizeof(c128);
   cudaStream_t s = c->stream;
   if (W) {
-    if (c->cfg.precision != PNGF_FP64) return PNGF_EINVAL;
+    if (c->cfg.precision == PNGF_MIXED) return PNGF_EINVAL;
     if (cudaMemcpy2DAsync(W, n * cs, at<c128>(c, c->L.W), (size_t)c->L.ldw * cs, n * cs, n,
                           cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return PNGF_ECUDA;
@@ -279,7 +298,7 @@ pngf_status pngf_snapshot(pngf_ctx* c) {
 
   cudaStream_t s = c->stream;
   size_t wbytes = L.snapW_bytes;
-  size_t wsrc = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
+  size_t wsrc = c->cfg.precision == PNGF_MIXED ? L.Wlo_re : L.W;
   if (cudaMemcpyAsync(c->ws + L.snapW, c->ws + wsrc, wbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(c->ws + L.snapState, c->ws + L.diag, L.state_bytes, cudaMemcpyDeviceToDevice, s) !=
           cudaSuccess ||
@@ -297,7 +316,7 @@ pngf_status pngf_restore(pngf_ctx* c) {
 
   cudaStream_t s = c->stream;
   size_t wbytes = L.snapW_bytes;
-  size_t wdst = c->cfg.precision == PNGF_FP64 ? L.W : L.Wlo_re;
+  size_t wdst = c->cfg.precision == PNGF_MIXED ? L.Wlo_re : L.W;
   // the control block is restored from its maintained fields on (f onwards): the
   // latched status and the barrier words stay as they are
   const size_t tail = offsetof(Control, f);
@@ -405,6 +424,7 @@ pngf_status pngf_set_launch(pngf_ctx* c, int32_t n_ctas, int32_t tensor_fold) {
 pngf_status pngf_gradient(pngf_ctx* c, double* grad, double* dodrho) {
   if (!c || !grad) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
+  if (c->cfg.precision == PNGF_PEC) return PNGF_EINVAL;
   return gradient(c, grad, dodrho);
 }
 
@@ -430,6 +450,7 @@ pngf_status pngf_set_state(pngf_ctx* c, const uint8_t* b, const double* W, const
                            const double* T, const double* o, int32_t since_refresh) {
   if (!c || !diag_W || !e || !T || !o || since_refresh < 0) return PNGF_EINVAL;
   if (!c->factored) return PNGF_ENOTFACTORED;
+  if (c->cfg.precision == PNGF_PEC) return PNGF_EINVAL;
   const bool fp64 = c->cfg.precision == PNGF_FP64;
   if (fp64 ? (!W || !b) : (W || b)) return PNGF_EINVAL;
   if (!fp64 && c->cfg.refresh_k > 0 && since_refresh >= c->cfg.refresh_k) return PNGF_EINVAL;

@@ -123,7 +123,7 @@ __device__ __forceinline__ void latch_status(Control* ctl, int s) {
 
 // ---------------------------------------------------------------- context
 struct Layout {
-  size_t W, LU, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, slots, actg, gsum, gsplit, xs, xadd, cbuf, ipiv, rbuf,
+  size_t W, LU, Q, pj, pR, pdiagH, Wlo_re, Wlo_im, X, xa, diag, e, T, v, b, pos_of, scr, part, rec, slots, actg, gsum, gsplit, xs, xadd, cbuf, ipiv, rbuf,
       snapW, snapState, ctl, total;
   size_t snapW_bytes;  // bytes of the maintained inverse copied by snapshot
   size_t tcimg, tcimgA_bytes, tcimg_bytes;  // mixed path: operand images of the tensor-core fold
@@ -182,6 +182,12 @@ pngf_status accept_flip(pngf_ctx* c, int pixel);
 pngf_status accept_flip_noalloc(pngf_ctx* c, int pixel);
 pngf_status set_wait_limit(pngf_ctx* c, unsigned long long polls, int hold_plus1);
 pngf_status import_finish(pngf_ctx* c, int since_refresh);
+// pec.cu
+pngf_status factor_pec(pngf_ctx* c, const uint8_t* b);
+pngf_status run_sweep_pec(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace, double* trace_f,
+                          int32_t trace_cap, int64_t* counters);
+pngf_status accept_flip_pec(pngf_ctx* c, int pixel);
+pngf_status score_flips_pec(pngf_ctx* c, const int32_t* pixels, int m, double* f_new);
 // gradient.cu
 pngf_status gradient(pngf_ctx* c, double* grad, double* dodrho);
 // general.cu
