@@ -378,6 +378,137 @@ def bench_batch(args, torch, dist, dev, P, Wl):
     return 0
 
 
+# ---------------------------------------------------------------- the other paths, one run each
+# name -> (what, case, extra): FP64-family searches and the gradient, each timed like the
+# headline (restore + one complete search per step, CUDA events on the launching stream)
+SIDE_WORKLOADS = {
+    "pec_fdfd128_nd1024": "perfect-conductor pixels (Eq. 2) on the 128^2 slab device, 32x32 region, FP64",
+    "tiles2x2_fdfd128_metal_nd1024": "2x2 tile flips (rank 4) on the 128^2 lossy-metal device, FP64",
+    "multifreq3_fdfd128_metal_nd1024": "3 frequencies (wavelengths 19, 20, 21 cells) sharing the design, "
+                                       "pixel flips, mean objective, FP64",
+    "gradient_fdfd256_nd4096": "objective gradient at a random design of the 64x64 region (mixed context)",
+}
+
+
+def bench_side(args, torch, dist, dev, P, Wl):
+    name = args.workload
+    stream = torch.cuda.Stream(dev)
+    peak_fp64 = fp64_peak_gflops(stream.cuda_stream)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sweeps = args.sweeps
+    ctxs, extra = [], {}
+    with torch.cuda.stream(stream):
+        if name == "gradient_fdfd256_nd4096":
+            case = Wl.get_case("fdfd256")
+            ctx = P.DbsContext(case, precision=P.PNGF_MIXED, device=str(dev), stream=stream)
+            ctx.factor(Wl.random_design(case.n_d, 0))
+            ctxs.append(ctx)
+            g = torch.empty(case.n_d, dtype=torch.float64, device=dev)
+            reps = 200
+
+            def step():
+                for _ in range(reps):
+                    P.pngf_gradient(ctx.ctx, g.data_ptr(), None)
+            units, unit, per = case.n_d * reps, "pixel gradients/s", reps
+        else:
+            base = "fdfd128_metal"
+            tau = 1e-6 if name.startswith("pec") else args.tau
+            if name.startswith("multifreq3"):
+                cases = [Wl.get_case(base + "_l19"), Wl.get_case(base), Wl.get_case(base + "_l21")]
+            else:
+                cases = [Wl.get_case(base)]
+            prec = P.PNGF_PEC if name.startswith("pec") else P.PNGF_FP64
+            b0 = Wl.random_design(cases[0].n_d, 0)
+            for c in cases:
+                cx = P.DbsContext(c, precision=prec, tau=tau, refresh_k=args.refresh_k, device=str(dev), stream=stream)
+                cx.factor(b0)
+                cx.snapshot()
+                ctxs.append(cx)
+            n = cases[0].n_d
+            cnt = torch.zeros(8, dtype=torch.int64, device=dev)
+            if name.startswith("pec"):
+                def step():
+                    P.pngf_restore(ctxs[0].ctx)
+                    P.pngf_dbs_sweep(ctxs[0].ctx, sweeps, None, None, None, 0, cnt.data_ptr())
+            else:
+                tiles = (Wl.square_tiles(32, 32, 2) if name.startswith("tiles")
+                         else np.arange(n, dtype=np.int32)[:, None])
+                ts = P.TileSearch(ctxs, tiles, combine=P.PNGF_COMBINE_MEAN)
+                extra["tile_m"], extra["n_tiles"], extra["systems"] = int(ts.tile_m), int(ts.n_tiles), len(ctxs)
+
+                def step():
+                    for cx in ctxs:
+                        P.pngf_restore(cx.ctx)
+                    P.pngf_dbs_sweep_tiles([cx.ctx for cx in ctxs], ts.combine, ts.tiles.data_ptr(), ts.n_tiles,
+                                           ts.tile_m, sweeps, None, None, None, 0, cnt.data_ptr(), ts.ws.data_ptr(),
+                                           ts.ws_bytes)
+            unit, per = UNIT, 1
+        for _ in range(max(args.warmup, 1)):
+            step()
+        stream.synchronize()
+        for cx in ctxs:
+            if cx.sync() != 0:
+                raise RuntimeError(f"{name}: warm-up failed")
+        if name != "gradient_fdfd256_nd4096":
+            c0 = cnt.cpu().numpy().copy()
+            units = float(c0[1])
+        torch.cuda.synchronize(dev)
+        clocks = Clocks(dist.local)
+        clocks.start()
+        time.sleep(0.3)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+    for cx in ctxs:
+        if cx.sync() != 0:
+            raise RuntimeError(f"{name}: timed steps failed")
+    ms = t0.elapsed_time(t1) / args.steps
+    value = units / (ms / 1e3)
+    if name == "gradient_fdfd256_nd4096":
+        n, n_o = 4096, 2
+        bytes_per = n * ((n_o + 2) * 16 + 8)  # T rows, e, dv read; grad written
+        gbs = bytes_per * reps / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "kernel": "gradient_kernel",
+                "note": "one launch reads (n_o + 2) x 16 B per pixel and writes 8 B (295 KB at N_d = 4096): "
+                        "L2-resident and launch-latency bound, not a bandwidth test"}
+        accepts = None
+        extra["us_per_gradient"] = ms * 1e3 / reps
+    else:
+        c1 = cnt.cpu().numpy()
+        accepts = int(c1[0])
+        tri = n * (n + 1) / 2
+        if name.startswith("pec"):
+            flops = accepts * (2 * 8.0 * tri + 8.0 * n * n)  # W and H triangles, Q full: one complex FMA each
+            kern = "dbs_pec_kernel"
+        else:
+            m = extra["tile_m"]
+            flops = accepts * len(ctxs) * 8.0 * m * tri  # rank-m update of every system's triangle
+            kern = "dbs_tiles_kernel"
+        gf = flops / (ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": gf / 1e3, "peak": peak_fp64 / 1e3, "unit": "TFLOP/s",
+                "frac": gf / peak_fp64, "traffic": None, "kernel": kern,
+                "peak_source": "FP64 FMA pipe, measured in this run by libpngf_peaks",
+                "work": "complex FMAs of the kept flips' updates (8 real flop each)"}
+    line = dict(metric=METRIC if unit == UNIT else "gradient throughput", value=value, unit=unit,
+                n_gpus=dist.world, steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config={"workload": name, "what": SIDE_WORKLOADS[name], "max_sweeps": sweeps,
+                        "step": "restore the factored start + one search (or %d gradients)" % per, **extra},
+                roofline=roof, accepts_per_step=accepts, clocks=clk, gpu_launches=args.steps * per,
+                cpu_baseline=None, e2e=None)
+    if dist.rank == 0:
+        print(json.dumps(line))
+    for cx in ctxs:
+        cx.close()
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 class RunSet:
     """B independent DBS runs (seeds seed0 .. seed0 + B - 1) on one device, each
@@ -532,6 +663,8 @@ def main():
 
     if args.workload == BATCH_WORKLOAD:
         return bench_batch(args, torch, dist, dev, P, Wl)
+    if args.workload in SIDE_WORKLOADS:
+        return bench_side(args, torch, dist, dev, P, Wl)
     case = Wl.get_case(case_name(args.workload))
     n, n_o = case.n_d, case.n_o
     prec = P.PNGF_MIXED if args.precision == "mixed" else P.PNGF_FP64

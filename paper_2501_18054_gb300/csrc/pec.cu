@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(kThreads) dbs_pec_kernel(const __grid_constant
     else if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EINVAL) status = PNGF_EINVAL;
   }
   int fi = 0;  // next entry of the forced list
-  while (!failed && status == PNGF_OK) {
+  // PNGF_ECAPACITY (set by CTA 0 alone) must not end one CTA's loop before the others'
+  while (!failed && (status == PNGF_OK || status == PNGF_ECAPACITY)) {
     const double f = s_f;
     const double thr = accept_threshold(s_op, f);
     if (forced) {

@@ -9,10 +9,21 @@ namespace pngf {
 namespace {
 
 constexpr int kThreads = 512;
-// Default bound of every device-side wait on other CTAs: 2^24 polls, each an L2
-// round trip plus (after the first few) a 32 ns back-off, on the order of ten
-// seconds.  pngf_set_wait_limit sets a context's own bound (Control::spin_limit).
+// Bound of every device-side wait on other CTAs: at most 2^24 polls (or a
+// context's own count, Control::spin_limit, set by pngf_set_wait_limit) and
+// at most kWaitNs of wall-clock time on the GPU's global timer, whichever
+// comes first.  The time cap matters: a poll is an L2 round trip plus a short
+// back-off, and under contention (every CTA of the grid polling one line) a
+// poll can take far longer than the uncontended ~1 us, so a bound in polls
+// alone can stretch to minutes.
 constexpr unsigned long long kSpinLimit = 1ull << 24;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned long long spin_limit_of(const Control* ctl) {
   const unsigned long long l = *reinterpret_cast<const volatile unsigned long long*>(&ctl->spin_limit);
@@ -102,8 +113,9 @@ __device__ bool grid_sync(Control* ctl) {
     const unsigned old = atomicAdd(&ctl->bar_count, 1u);
     const unsigned target = (old / P + 1) * P;
     unsigned long long it = 0;
+    const unsigned long long t0 = global_ns();
     while ((int)(ld_volatile(&ctl->bar_count) - target) < 0) {
-      if (++it > lim) {
+      if (++it > lim || ((it & 63) == 0 && global_ns() - t0 > kWaitNs)) {
         latch_status(ctl, PNGF_ETIMEOUT);
         ok = 0;
         break;
@@ -123,8 +135,8 @@ __device__ bool grid_sync(Control* ctl) {
 // waits for it run out and latch PNGF_ETIMEOUT.  One-shot: the hold is cleared.
 __device__ void hold_if_asked(Control* ctl) {
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&ctl->hold_cta) == (int)blockIdx.x + 1) {
-    const unsigned long long lim = 4 * spin_limit_of(ctl);
-    for (unsigned long long it = 0; it < lim; ++it) {
+    const unsigned long long lim = 4 * spin_limit_of(ctl), t0 = global_ns();
+    for (unsigned long long it = 0; it < lim && global_ns() - t0 < 4 * kWaitNs; ++it) {
       if (*reinterpret_cast<volatile int*>(&ctl->hold_flag) != 0) break;
       __nanosleep(256);
     }

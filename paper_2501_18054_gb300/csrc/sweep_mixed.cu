@@ -135,10 +135,11 @@ __device__ __forceinline__ dd improve_bound(dd f, dd tau) {
 __device__ __forceinline__ long long poll_word(const unsigned long long* w, unsigned seq, bool& ok,
                                                unsigned long long lim) {
   unsigned long long it = 0;
+  const unsigned long long t0 = global_ns();
   for (;;) {
     unsigned long long v = *reinterpret_cast<const volatile unsigned long long*>(w);
     if ((unsigned)(v >> kSeqShift) == seq) return (long long)(v & kKeyMask);
-    if (++it > lim) {
+    if (++it > lim || ((it & 63) == 0 && global_ns() - t0 > kWaitNs)) {
       ok = false;
       return kNoCand;
     }

@@ -151,3 +151,23 @@ def test_pec_unavailable_calls(P):
     with pytest.raises(P.PngfError):
         ctx.score_flips([0, 1], want_ports=True)
     ctx.close()
+
+
+def test_pec_trace_capacity_completes_the_search(P):
+    """A trace shorter than the run (here none at all) ends nothing early: the
+    search completes with PNGF_ECAPACITY reported and the oracle's end state."""
+    case = _case("fdfd64")
+    b0 = W.random_design(case.n_d, 0)
+    ref = O.dbs(O.Problem.from_case(case), b0, W.raster_order(case.n_d, 6), tau=1e-6, evaluator=O.evaluate_pec)
+    for cap in (0, 5):
+        ctx = P.DbsContext(case, precision=P.PNGF_PEC, tau=1e-6)
+        ctx.factor(b0)
+        if cap == 0:
+            P.pngf_dbs_sweep(ctx.ctx, 6, None, None, None, 0, ctx.counters.data_ptr())
+            assert ctx.sync() == P.PNGF_OK
+            c = ctx.counters.cpu().numpy()
+        else:
+            c = ctx.dbs_sweep(6, trace_cap=cap)["counters"]
+        assert c[0] == len(ref.accepted) and c[6] == P.PNGF_ECAPACITY
+        assert np.array_equal(ctx.design(), ref.b)
+        ctx.close()

@@ -158,3 +158,15 @@ def test_tile_arguments_are_checked(P):
     assert ctxs[0].sync() == P.PNGF_EINVAL
     mixed.close()
     ctxs[0].close()
+
+
+def test_tile_trace_capacity_completes_the_search(P):
+    tiles = _tiles("square")
+    b0 = W.random_design(100, 0)
+    cases, ctxs = _systems(P, ["fdfd64"], b0)
+    ref = O.dbs_tiles([O.Problem.from_case(cases[0])], b0, tiles, W.raster_order(len(tiles), 8), tau=1e-9)
+    ts = P.TileSearch(ctxs, tiles)
+    res = ts.dbs_sweep(8, trace_cap=3)
+    assert res["counters"][0] == len(ref.accepted) and res["counters"][6] == P.PNGF_ECAPACITY
+    assert np.array_equal(ctxs[0].design(), ref.b)
+    ctxs[0].close()
