@@ -12,12 +12,13 @@
 // FP64 rate is about 1.2 TFLOP/s, so every kernel here is FP64-pipe bound.
 #include <cstdio>
 
-#include "pngf_internal.cuh"
+#include "sweep_common.cuh"
 
 namespace pngf {
 namespace {
 
 constexpr int NB = 32;  // panel width / block size of the substitutions
+constexpr int kCoopPanelRows = 256;  // taller panels are factored by many CTAs
 
 // ---------------------------------------------------------------- M = I - G V
 __global__ void build_system(const c128* __restrict__ G, const c128* __restrict__ dv,
@@ -122,6 +123,119 @@ __global__ void __launch_bounds__(1024) panel_factor(c128* __restrict__ A, int n
       }
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- panel, many CTAs
+// The same factorisation of rows [j0, n) x columns [j0, j0+jb) spread over a
+// cooperative grid: CTA q owns a contiguous chunk of the rows.  Per column:
+// every CTA reduces the CTAs' candidates (same fixed order everywhere: the
+// same pivot), the owners of the pivot row and of the diagonal row stage
+// them, a grid barrier, the swap and the update of every CTA's own rows
+// (tracking the next column's candidate), a grid barrier.  The FP64 work of a
+// panel is spread over the SMs instead of one, where a single CTA is held to
+// one SM's share of the FP64 pipe.
+constexpr int PC_THREADS = 256;
+
+__device__ __forceinline__ void pc_better(double& v, long long& i, double ov, long long oi) {
+  if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+}
+
+__global__ void __launch_bounds__(PC_THREADS) panel_factor_coop(c128* __restrict__ A, int n, int lda, int j0, int jb,
+                                                                int* __restrict__ ipiv, Control* __restrict__ ctl,
+                                                                double* __restrict__ pv, long long* __restrict__ pi,
+                                                                c128* __restrict__ rowbuf) {
+  __shared__ double red_v[PC_THREADS / 32];
+  __shared__ long long red_i[PC_THREADS / 32];
+  __shared__ c128 urow[NB];
+  __shared__ int piv_s;
+  const int P = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rows = n - j0;
+  const int rb = j0 + (int)((long long)rows * cta / P), re = j0 + (int)((long long)rows * (cta + 1) / P);
+  const bool active_lane = lane < jb;
+  // this CTA's candidate for column j0
+  {
+    double v = -1.0;
+    long long idx = LLONG_MAX;
+    for (int r = rb + tid; r < re; r += blockDim.x) pc_better(v, idx, cabs1(A[(size_t)r * lda + j0]), r);
+    for (int off = 16; off > 0; off >>= 1)
+      pc_better(v, idx, __shfl_xor_sync(0xffffffffu, v, off), __shfl_xor_sync(0xffffffffu, idx, off));
+    if (lane == 0) { red_v[warp] = v; red_i[warp] = idx; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < PC_THREADS / 32; ++w) pc_better(v, idx, red_v[w], red_i[w]);
+      pv[cta] = v;
+      pi[cta] = idx;
+    }
+  }
+  if (!grid_sync(ctl)) return;
+  for (int jj = 0; jj < jb; ++jj) {
+    const int col = j0 + jj, par = jj & 1;
+    // ---- the pivot: every CTA reduces the P candidates in the same order
+    double v = -1.0;
+    long long idx = LLONG_MAX;
+    for (int q = tid; q < P; q += blockDim.x) pc_better(v, idx, pv[par * P + q], pi[par * P + q]);
+    for (int off = 16; off > 0; off >>= 1)
+      pc_better(v, idx, __shfl_xor_sync(0xffffffffu, v, off), __shfl_xor_sync(0xffffffffu, idx, off));
+    __syncthreads();
+    if (lane == 0) { red_v[warp] = v; red_i[warp] = idx; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < PC_THREADS / 32; ++w) pc_better(v, idx, red_v[w], red_i[w]);
+      int p = (int)idx;
+      if (!(v > 0.0)) {  // exact zero (or NaN) column: singular
+        if (cta == 0) latch_status(ctl, PNGF_ESINGULAR);
+        p = col;
+      }
+      piv_s = p;
+      if (cta == 0) ipiv[col] = p;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    // ---- stage the pivot row (slot 0) and the diagonal row (slot 1)
+    if (p >= rb && p < re && tid < jb) rowbuf[tid] = A[(size_t)p * lda + j0 + tid];
+    if (col >= rb && col < re && tid < jb) rowbuf[NB + tid] = A[(size_t)col * lda + j0 + tid];
+    if (!grid_sync(ctl)) return;
+    if (tid < jb) urow[tid] = rowbuf[tid];
+    if (p != col) {
+      if (col >= rb && col < re && tid < jb) A[(size_t)col * lda + j0 + tid] = rowbuf[tid];
+      if (p >= rb && p < re && tid < jb) A[(size_t)p * lda + j0 + tid] = rowbuf[NB + tid];
+    }
+    __syncthreads();
+    // ---- scale column col below the diagonal, update the trailing panel
+    //      columns of the own rows, track the next column's candidate
+    const c128 inv = cdiv(mk(1.0, 0.0), urow[jj]);
+    const c128 u = active_lane ? urow[lane] : mk(0.0, 0.0);
+    double bv = -1.0;
+    long long bi = LLONG_MAX;
+    for (int r = max(rb, col + 1) + warp; r < re; r += PC_THREADS / 32) {
+      c128* row = A + (size_t)r * lda + j0;
+      const c128 a = active_lane ? row[lane] : mk(0.0, 0.0);
+      const double lx = __shfl_sync(0xffffffffu, a.x, jj);
+      const double ly = __shfl_sync(0xffffffffu, a.y, jj);
+      const c128 lr = cmul(mk(lx, ly), inv);
+      if (lane == jj) {
+        row[lane] = lr;
+      } else if (active_lane && lane > jj) {
+        const c128 na = cfms(lr, u, a);
+        row[lane] = na;
+        if (lane == jj + 1) pc_better(bv, bi, cabs1(na), r);
+      }
+    }
+    if (jj + 1 < jb) {
+      // lane jj + 1 of each warp holds the warp's candidate
+      bv = __shfl_sync(0xffffffffu, bv, jj + 1);
+      bi = __shfl_sync(0xffffffffu, bi, jj + 1);
+      __syncthreads();
+      if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < PC_THREADS / 32; ++w) pc_better(bv, bi, red_v[w], red_i[w]);
+        pv[(par ^ 1) * P + cta] = bv;
+        pi[(par ^ 1) * P + cta] = bi;
+      }
+    }
+    if (!grid_sync(ctl)) return;
   }
 }
 
@@ -402,7 +516,21 @@ pngf_status factor_fp64(pngf_ctx* c, const uint8_t* b) {
   // LU with partial pivoting
   for (int j0 = 0; j0 < n; j0 += NB) {
     int jb = n - j0 < NB ? n - j0 : NB;
-    panel_factor<<<1, 1024, 0, s>>>(LU, n, ldw, j0, jb, ipiv, ctl);
+    const int rows = n - j0;
+    if (rows > kCoopPanelRows) {
+      int P = (rows + 31) / 32;
+      if (P > c->n_sm) P = c->n_sm;
+      if (cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned), s) != cudaSuccess) return PNGF_ECUDA;
+      double* pv = reinterpret_cast<double*>(c->ws + c->L.part + 2 * (size_t)c->L.n_part * sizeof(long long));
+      long long* pi = reinterpret_cast<long long*>(c->ws + c->L.part);
+      c128* rowbuf = at<c128>(c, c->L.rbuf);
+      void* params[] = {&LU, (void*)&n, (void*)&ldw, &j0, &jb, &ipiv, &ctl, &pv, &pi, &rowbuf};
+      if (cudaLaunchCooperativeKernel((const void*)panel_factor_coop, dim3(P), dim3(PC_THREADS), params, 0, s) !=
+          cudaSuccess)
+        return PNGF_ECUDA;
+    } else {
+      panel_factor<<<1, 1024, 0, s>>>(LU, n, ldw, j0, jb, ipiv, ctl);
+    }
     apply_swaps<<<(n + 255) / 256, 256, 0, s>>>(LU, n, ldw, j0, jb, ipiv);
     int rest = n - j0 - jb;
     if (rest > 0) {

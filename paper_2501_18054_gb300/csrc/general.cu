@@ -166,6 +166,32 @@ __device__ bool score_tile_sys(const SweepArgs& a, const ObjParams& op, const c1
   return true;
 }
 
+// Single-pixel tiles (tile_m = 1), one thread per candidate: the same
+// arithmetic as the warp path for m = 1 (pivot 1 - delta W_kk, its reciprocal,
+// then (delta e_k) times it), so both paths take the same decisions.
+__device__ bool score_pixel_tile(const GenArgs& g, const c128 (*s_o)[kMaxPorts], int t, double& F) {
+  const int k = g.tiles[t];
+  if (k < -1 || k >= g.sys[0].n) {
+    latch_status(g.sys[0].ctl, PNGF_EINVAL);
+    return false;
+  }
+  if (k < 0) return false;
+  double fs[kMaxSys];
+  for (int s = 0; s < g.n_sys; ++s) {
+    const SweepArgs& a = g.sys[s];
+    const c128 dl = delta_of(a, k);
+    const c128 A = csub(mk(1.0, 0.0), cmul(dl, a.diag[k]));
+    if (!(cabs2(A) >= 1e-28)) return false;
+    const c128 y = cmul(cmul(dl, a.e[k]), cdiv(mk(1.0, 0.0), A));
+    double f = 0.0;
+#pragma unroll 1
+    for (int p = 0; p < a.n_o; ++p) f += objective_term(a.op, p, cadd(s_o[s][p], cmul(a.T[(size_t)p * a.ldt + k], y)));
+    fs[s] = f;
+  }
+  F = combine_of(fs, g.n_sys, g.combine, g.kind);
+  return true;
+}
+
 // combined objective of flipping tile t (one warp); false if any system is singular
 __device__ bool score_tile(const GenArgs& g, const c128 (*s_o)[kMaxPorts], int t, c128* buf, double& F,
                            double* f_sys) {
@@ -280,28 +306,30 @@ __global__ void __launch_bounds__(kThreads) dbs_tiles_kernel(const __grid_consta
     const double thr = g.tau * fmax(fabs(F), 1e-30);
     // ---- score this CTA's tiles (one warp per tile), reduce to the CTA's candidate
     if (!forced) {
+      const bool px1 = M == 1;  // single-pixel tiles: one thread per candidate
+      const int t0 = px1 ? tid : warp, ts = px1 ? (int)blockDim.x : kWarps;
       if (g.mode == PNGF_FIRST_IMPROVEMENT) {
         long long best = LLONG_MAX;
-        for (int ti = tb + warp; ti < te; ti += kWarps) {
+        for (int ti = tb + t0; ti < te; ti += ts) {
           const int pos = g.order ? g.pos_of[ti] : ti;
           if (pos < t || pos >= best) continue;
           double Fn;
-          if (!score_tile(g, s_o, ti, wbuf, Fn, nullptr)) continue;
+          if (!(px1 ? score_pixel_tile(g, s_o, ti, Fn) : score_tile(g, s_o, ti, wbuf, Fn, nullptr))) continue;
           const double gain = g.kind == PNGF_OBJ_MAX_WEIGHTED_POWER ? Fn - F : F - Fn;
           if (gain - thr > 0.0) best = pos;
         }
-        best = block_min_ll(lane == 0 ? best : LLONG_MAX);
+        best = block_min_ll(px1 || lane == 0 ? best : LLONG_MAX);
         if (tid == 0) sel_offer(ctl, rd, best, cta);
       } else {
         double gb = -INFINITY;
         int pix = INT_MAX;
-        for (int ti = tb + warp; ti < te; ti += kWarps) {
+        for (int ti = tb + t0; ti < te; ti += ts) {
           double Fn;
-          if (!score_tile(g, s_o, ti, wbuf, Fn, nullptr)) continue;
+          if (!(px1 ? score_pixel_tile(g, s_o, ti, Fn) : score_tile(g, s_o, ti, wbuf, Fn, nullptr))) continue;
           const double gain = g.kind == PNGF_OBJ_MAX_WEIGHTED_POWER ? Fn - F : F - Fn;
           if (better(gain, ti, gb, pix)) { gb = gain; pix = ti; }
         }
-        if (lane != 0) { gb = -INFINITY; pix = INT_MAX; }
+        if (!px1 && lane != 0) { gb = -INFINITY; pix = INT_MAX; }
         block_best(gb, pix);
         if (tid == 0) {
           g.part_gain[slot * P + cta] = gb;
