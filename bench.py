@@ -378,6 +378,22 @@ def bench_batch(args, torch, dist, dev, P, Wl):
     return 0
 
 
+def mixed_alg_bytes(c2, n, n_o) -> float:
+    """Algorithmic HBM bytes of the mixed search's launches, from their counters
+    (rows: runs; [0] kept flips, [1] evaluations, [4] refreshes, [5] folds,
+    [7] active pixels summed over the refreshes): per fold the upper triangle of
+    the two FP32 planes read + written (16 B per element); per refresh with m
+    active pixels the m rows of G as FP32 pairs (16 B x m x n), the FP32 upper
+    triangle (8 B) and its entries in the active rows above each column strip
+    (8 B x m / n per element); per kept flip one column of the FP32 planes
+    (8 B x n); per evaluation (3 + n_o) x 16 B of state."""
+    c2 = np.atleast_2d(c2)
+    tri = n * (n + 1) / 2
+    n_flush, n_ref, sum_m = float(c2[:, 5].sum()), float(c2[:, 4].sum()), float(c2[:, 7].sum())
+    return (n_flush * 16.0 * tri + 16.0 * n * sum_m + n_ref * 8.0 * tri + 8.0 * tri * sum_m / n
+            + float(c2[:, 0].sum()) * 8.0 * n + float(c2[:, 1].sum()) * (3 + n_o) * 16.0)
+
+
 # ---------------------------------------------------------------- the other paths, one run each
 # name -> (what, case, extra): FP64-family searches and the gradient, each timed like the
 # headline (restore + one complete search per step, CUDA events on the launching stream)
@@ -387,7 +403,87 @@ SIDE_WORKLOADS = {
     "multifreq3_fdfd128_metal_nd1024": "3 frequencies (wavelengths 19, 20, 21 cells) sharing the design, "
                                        "pixel flips, mean objective, FP64",
     "gradient_fdfd256_nd4096": "objective gradient at a random design of the 64x64 region (mixed context)",
+    "hankel128_nd16384": "closed-form 2D Green function, 128x128 region (N_d = 16384), 4 ring ports, mixed "
+                         "precision, one run on all SMs",
 }
+
+
+def bench_hankel(args, torch, dist, dev, P, Wl):
+    """The largest region: one mixed run (R = 64, refresh every 64 kept flips), the
+    final design's S-parameters checked against one oracle solve of that design."""
+    import oracle as O
+    case = Wl.get_case("hankel128")
+    n, n_o = case.n_d, case.n_o
+    stream = torch.cuda.Stream(dev)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    with torch.cuda.stream(stream):
+        ctx = P.DbsContext(case, precision=P.PNGF_MIXED, tau=args.tau, refresh_k=args.refresh_k,
+                           delay_r=args.delay_r, tensor_fold=args.tensor_fold, device=str(dev), stream=stream)
+        b0 = Wl.random_design(n, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.factor(b0)
+        e1.record(stream)
+        stream.synchronize()
+        factor_ms = e0.elapsed_time(e1)
+        if ctx.sync() != 0:
+            raise RuntimeError("hankel: factor failed")
+        ctx.snapshot()
+        cnt = torch.zeros(8, dtype=torch.int64, device=dev)
+
+        def step():
+            P.pngf_restore(ctx.ctx)
+            P.pngf_dbs_sweep(ctx.ctx, args.sweeps, None, None, None, 0, cnt.data_ptr())
+
+        for _ in range(max(args.warmup, 1)):
+            step()
+        stream.synchronize()
+        if ctx.sync() != 0:
+            raise RuntimeError("hankel: warm-up failed")
+        clocks = Clocks(dist.local)
+        clocks.start()
+        time.sleep(0.3)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+    if ctx.sync() != 0:
+        raise RuntimeError("hankel: timed steps failed")
+    ms = t0.elapsed_time(t1) / args.steps
+    c2 = cnt.cpu().numpy()
+    value = float(c2[1]) / (ms / 1e3)
+    bytes_alg = mixed_alg_bytes(c2, n, n_o)
+    gbs = bytes_alg / (ms / 1e3) / 1e9
+    o_gpu, _ = ctx.eval_ports()
+    b_end = ctx.design()
+    ts = time.perf_counter()
+    ev = O.evaluate(O.Problem.from_case(case), b_end)
+    oracle_s = time.perf_counter() - ts
+    S_ex = (ev.o - case.s_off) * case.s_scale
+    S_g = (o_gpu - case.s_off) * case.s_scale
+    s_err = float(np.max(np.abs(S_g - S_ex) / np.maximum(np.abs(S_ex), 1e-3)))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=dist.world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
+                data="synthetic",
+                config={"workload": "hankel128_nd16384", "what": SIDE_WORKLOADS["hankel128_nd16384"], "n_d": n,
+                        "n_o": n_o, "runs": 1, "max_sweeps": args.sweeps, "refresh_k": args.refresh_k,
+                        "delay_r": args.delay_r, "step": "restore the factored start + one search",
+                        "note": "the configuration's 16 batched runs do not fit at once: each mixed context "
+                                "holds ~20 GB (FP64 factor scratch included), and each FP64 factor takes "
+                                "tens of seconds; one run is measured"},
+                roofline={"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                          "traffic": None, "kernel": "dbs_mixed_kernel", "algorithmic_bytes_per_step": bytes_alg},
+                accepts_per_step=int(c2[0]), evals_per_step=int(c2[1]), refreshes=int(c2[4]), folds=int(c2[5]),
+                factor_ms=factor_ms, s_param_rel_err_vs_oracle=s_err, oracle_solve_s=oracle_s, clocks=clk,
+                gpu_launches=args.steps, cpu_baseline=None, e2e=None)
+    if dist.rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
 
 
 def bench_side(args, torch, dist, dev, P, Wl):
@@ -663,6 +759,8 @@ def main():
 
     if args.workload == BATCH_WORKLOAD:
         return bench_batch(args, torch, dist, dev, P, Wl)
+    if args.workload == "hankel128_nd16384":
+        return bench_hankel(args, torch, dist, dev, P, Wl)
     if args.workload in SIDE_WORKLOADS:
         return bench_side(args, torch, dist, dev, P, Wl)
     case = Wl.get_case(case_name(args.workload))
@@ -753,9 +851,7 @@ def main():
         # active rows above each column strip (8 B x m / n per element); per kept flip
         # one column of the FP32 planes (8 B x n); per evaluation (3 + n_o) x 16 B of
         # FP64 state.
-        n_flush, n_ref, sum_m = int(c2[:, 5].sum()), int(c2[:, 4].sum()), float(c2[:, 7].sum())
-        bytes_alg = (n_flush * 16.0 * tri + 16.0 * n * sum_m + n_ref * 8.0 * tri + 8.0 * tri * sum_m / n
-                     + acc_per_step * 8.0 * n + evals_per_step * (3 + n_o) * 16.0)
+        bytes_alg = mixed_alg_bytes(c2, n, n_o)
         gbs = bytes_alg / (step_ms / 1e3) / 1e9
         traffic, traffic_note = None, "no capture of the current kernel sources"
         if args.workload == TRAFFIC_CAPTURE["workload"] and sources_fingerprint() == TRAFFIC_CAPTURE["sources_sha256"]:

@@ -473,7 +473,8 @@ WORKLOADS = {
 def get_case(name: str) -> Case:
     if name.startswith("hankel"):
         side = int(name[len("hankel"):] or 128)
-        return make_hankel_case(side)
+        # a large closed-form G is faster to rebuild (~15 s at 128 x 128) than to cache (4.3 GB)
+        return make_hankel_case(side, cache=side <= 64)
     return make_fdfd_case(name)
 
 
