@@ -67,7 +67,11 @@ typedef enum {
   PNGF_ENOTFACTORED = 5,  /* pngf_factor has not run on this context */
   PNGF_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
   PNGF_ENUMERIC = 7,      /* non-finite value met on the device */
-  PNGF_ECAPACITY = 8      /* trace buffer full (the sweep stopped early) */
+  PNGF_ECAPACITY = 8,     /* trace buffer full (kept flips past it are applied, not recorded) */
+  PNGF_EACCURACY = 9      /* PNGF_MIXED: a refresh found the field's residual above 1e-3 of the
+                             field (the FP32 maintained inverse lost accuracy: an ill-conditioned
+                             system, such as a design driven into a high-Q resonance); the search
+                             stops and its state is not to be trusted: use PNGF_FP64 */
 } pngf_status;
 
 /* PNGF_FP64: every step in FP64.  PNGF_MIXED: an FP32 maintained inverse with a

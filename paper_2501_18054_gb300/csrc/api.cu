@@ -482,6 +482,7 @@ const char* pngf_status_string(pngf_status s) {
     case PNGF_ETIMEOUT: return "device wait timed out";
     case PNGF_ENUMERIC: return "non-finite value";
     case PNGF_ECAPACITY: return "trace buffer full";
+    case PNGF_EACCURACY: return "mixed precision lost accuracy (ill-conditioned system)";
   }
   return "unknown status";
 }

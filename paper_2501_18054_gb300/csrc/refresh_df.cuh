@@ -146,6 +146,7 @@ __device__ void refresh_x_df(const SweepArgs& a, int pb, int pe, const int* act,
 // area, area_bytes: 16-byte aligned shared memory for the ring (the partial
 // sums reuse it: blockDim float4).
 constexpr int RD_D = 4;
+constexpr float kRefreshGuard = 1e-3f;  // largest relative residual of e the mixed search accepts
 constexpr int RD_RMAX = 8;
 // list entries per group and stage for own rows and NV vectors in area_bytes (0: too small)
 __host__ __device__ __forceinline__ int rd_rows(int own, int NV, int nthreads, unsigned area_bytes) {
@@ -224,6 +225,8 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
     }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+  __shared__ unsigned s_rmax, s_ymax;  // non-negative FP32 magnitudes as ordered bit patterns
+  if (tid == 0) s_rmax = s_ymax = 0u;
   __syncthreads();
   float4* part = reinterpret_cast<float4*>(area);
 #pragma unroll
@@ -247,11 +250,22 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
       const c128 y = q == 0 ? a.e[j] : a.T[(size_t)(q - 1) * a.ldt + j];
       const c128 r = cadd(csub(rhs, y), mk(df_value(re), df_value(im)));
       rvec(a, 0, q)[j] = r;
+      if (q == 0) {  // accuracy guard on the field's residual
+        atomicMax(&s_rmax, __float_as_uint((float)cabs1(r)));
+        atomicMax(&s_ymax, __float_as_uint((float)cabs1(y)));
+      }
       const c128 x2 = cmul(a.v[j], r);
       x2f(a, q)[j] = make_float2((float)x2.x, (float)x2.y);
     }
     __syncthreads();
   }
+  // The refresh corrects e and T by one refinement step with the FP32 inverse,
+  // which converges only while |r| stays far below |e|: between refreshes the
+  // FP32 drift leaves |r| ~ 1e-7 |e| on well-conditioned systems.  A residual
+  // above kRefreshGuard |e| (an ill-conditioned system, e.g. a design driven
+  // into a high-Q resonance) means the maintained state has lost accuracy.
+  if (tid == 0 && __uint_as_float(s_rmax) > kRefreshGuard * __uint_as_float(s_ymax))
+    latch_status(a.ctl, PNGF_EACCURACY);
 }
 
 __device__ void refresh_residual_df(const SweepArgs& a, int pb, int pe, const int* act, int m, unsigned char* area,

@@ -617,6 +617,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         refresh_residual_df(a, pb, pe, act, m_act, work + rd_list_bytes(n), (unsigned)(kMixedWork - rd_list_bytes(n)));
         const int t_end = count_below(act, m_act, pe - 1);
         if (!grid_sync(ctl)) { failed = true; break; }
+        // the accuracy guard of any CTA ends the search in every CTA (read after the barrier)
+        if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EACCURACY) {
+          status = PNGF_EACCURACY;
+          break;
+        }
         tick(9);
         correct_strips<true>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(work),
                              (int)(dynamic_smem_bytes() - kOwnStateSmem));
@@ -677,7 +682,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     for (int q = 0; q < 16; ++q) ctl->phase_cycles[q] = ph[q];
     if (a.counters)
       for (int q = 0; q < 8; ++q) a.counters[q] = ctl->counters[q];
-    if (status == PNGF_ENUMERIC || status == PNGF_ETIMEOUT || status == PNGF_EINVAL) latch_status(ctl, status);
+    if (status == PNGF_ENUMERIC || status == PNGF_ETIMEOUT || status == PNGF_EINVAL || status == PNGF_EACCURACY)
+      latch_status(ctl, status);
   }
 }
 

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpngf.so")
 
 PNGF_OK, PNGF_EINVAL, PNGF_ENOMEM, PNGF_ECUDA, PNGF_ESINGULAR = 0, 1, 2, 3, 4
-PNGF_ENOTFACTORED, PNGF_ETIMEOUT, PNGF_ENUMERIC, PNGF_ECAPACITY = 5, 6, 7, 8
+PNGF_ENOTFACTORED, PNGF_ETIMEOUT, PNGF_ENUMERIC, PNGF_ECAPACITY, PNGF_EACCURACY = 5, 6, 7, 8, 9
 PNGF_FP64, PNGF_MIXED, PNGF_PEC = 0, 1, 2
 PNGF_FIRST_IMPROVEMENT, PNGF_BEST_IMPROVEMENT = 0, 1
 PNGF_OBJ_MAX_WEIGHTED_POWER, PNGF_OBJ_MIN_INSERTION_LOSS = 0, 1

@@ -191,3 +191,26 @@ def test_batch_call_captured_in_cuda_graph(P, fdfd64):
             assert np.array_equal(o, o2) and f == f2
     for cx in ctxs:
         cx.close()
+
+
+def test_mixed_accuracy_guard_stops_a_broken_state(P, fdfd64):
+    """A mixed search whose maintained field no longer solves the system (here a
+    checkpoint imported with e scaled by 1.5, a host-side stand-in for an FP32
+    inverse that lost accuracy on an ill-conditioned system) stops at its next
+    refresh with PNGF_EACCURACY instead of searching on a wrong state."""
+    ctx = P.DbsContext(fdfd64, precision=P.PNGF_MIXED, tau=1e-9, delay_r=8, refresh_k=16, tensor_fold=1)
+    ctx.factor(W.random_design(fdfd64.n_d, 0))
+    ck = ctx.checkpoint()
+    ck["e"] = ck["e"] * 1.5
+    ck["since_refresh"] = 0
+    ctx.set_state(ck)
+    ctx.dbs_sweep(3, sync=False)
+    assert ctx.sync() == P.PNGF_EACCURACY
+    c = ctx.counters.cpu().numpy()
+    assert c[6] == P.PNGF_EACCURACY and c[0] == 16  # stopped at the first refresh
+    # the same context with a sound state searches normally
+    ctx.factor(W.random_design(fdfd64.n_d, 0))
+    g = _golden("fdfd64_first_raster")
+    res = ctx.dbs_sweep(g["spec"]["n_sweeps"])
+    assert _seq(res["trace"]) == [tuple(a[:3]) for a in g["accepted"]]
+    ctx.close()
