@@ -120,7 +120,7 @@ __device__ bool grid_sync(Control* ctl) {
         ok = 0;
         break;
       }
-      if (it > 32) __nanosleep(32);
+      if (it > 256) __nanosleep(32);
     }
     fence_acq_rel_gpu();  // acquire: every CTA's writes before the others' arrivals
     s_ok = ok;

@@ -143,7 +143,7 @@ __device__ __forceinline__ long long poll_word(const unsigned long long* w, unsi
       ok = false;
       return kNoCand;
     }
-    if (it > 64) __nanosleep(32);
+    if (it > 1024) __nanosleep(32);  // the awaited word usually lands within a few round trips
   }
 }
 
@@ -332,9 +332,16 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           const dd iz = dd_rcp(z2);
           al = cdd{dd_mul(z.re, iz), dd_neg(dd_mul(z.im, iz))};
           co = cdd_mul(al, s_e[tid]);
+          // ports two at a time: their |S_p(new)|^2 chains are independent, the
+          // objective still adds them in port order
+          int p = 0;
 #pragma unroll 1
-          for (int p = 0; p < n_o; ++p)
-            fn = obj_acc<OBJ>(s_w[p], cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
+          for (; p + 1 < n_o; p += 2) {
+            const dd a0 = cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p]));
+            const dd a1 = cdd_abs2(cdd_fma(co, s_T[(p + 1) * kOwnMax + tid], s_S[p + 1]));
+            fn = obj_acc<OBJ>(s_w[p + 1], a1, obj_acc<OBJ>(s_w[p], a0, fn));
+          }
+          if (p < n_o) fn = obj_acc<OBJ>(s_w[p], cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
           ok = true;
         }
       }
