@@ -714,7 +714,7 @@ def autotune_launch(args, torch, P, Wl, case, dev, nsm, tstream):
     designs must equal the FP64 path's from the same starts, with S within 1e-4."""
     import argparse
     from paper_2501_18054_gb300 import autotune as A
-    cands = A.candidates(case.n_d, nsm, args.refresh_k, runs_options=(1, 2, 4), delay_options=(32, 64))
+    cands = A.candidates(case.n_d, nsm, args.refresh_k, runs_options=(1, 2, 4, 6, 8), delay_options=(32, 64))
     max_runs = max(c.runs for c in cands)
     seeds = list(range(max_runs))
     ref = RunSet(torch, P, Wl, case, dev, P.PNGF_FP64, args, seeds, nsm // max_runs, tstream)

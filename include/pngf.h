@@ -207,8 +207,9 @@ pngf_status pngf_accept_flip_noalloc(pngf_ctx* ctx, int32_t pixel);
  * Kept flips past trace_cap are still applied but not recorded; [6] is then
  * PNGF_ECAPACITY.  The state stays on the device for further calls.
  * Mixed precision keeps each CTA's share of the pixels in shared memory:
- * N_d must not exceed 128 x the persistent grid (one CTA per SM, or n_ctas),
- * else PNGF_EINVAL before any launch.
+ * with own = ceil(N_d / grid) (grid = one CTA per SM, or n_ctas) rounded up
+ * to 32, own <= 256 and (delay_r + 8) x own x 8 bytes <= 144 KiB (the
+ * delayed rows and partial sums), else PNGF_EINVAL before any launch.
  */
 pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order,
                            int32_t* trace, double* trace_f, int32_t trace_cap,

@@ -12,11 +12,12 @@ free and is chosen here from timed trials:
                   CUDA cores.
 
 A candidate is admissible when its launch can hold the region: the mixed
-search keeps each CTA's share of the pixels in shared memory
-(``own_max`` = 128 per CTA).  A trial is accurate when every run ends on the
-same final design as the FP64 path from the same start and its S-parameters
-are within the accuracy bar (1e-4 relative) of the FP64 path's; only
-accurate trials are eligible.  The search is successive halving: every
+search keeps each CTA's share of the pixels in shared memory (at most
+``own_max`` = 256 per CTA), and between folds their delayed rows and partial
+sums, (R + 8) x own (rounded up to 32) x 8 bytes, in a 144 KB work area.  A
+trial is accurate when every run ends on the same final design as the FP64
+path from the same start and its S-parameters are within the accuracy bar
+(1e-4 relative) of the FP64 path's; only accurate trials are eligible.  The search is successive halving: every
 candidate is timed briefly, the fastest third is timed again with more steps,
 and the fastest of those wins (ties: fewer runs, then the smaller delay, then
 the tensor-core fold).
@@ -61,9 +62,21 @@ class Trial:
         return d
 
 
+WORK_BYTES = 147456  # the mixed search's shared-memory work area
+PARTS_MAX = 8
+
+
+def delayed_fits(n_d: int, ctas: int, r: int, work_bytes: int = WORK_BYTES) -> bool:
+    """The delayed rows (r per pixel) and the delayed sum's partials of the
+    largest CTA share fit in the work area."""
+    own = -(-n_d // ctas)
+    oss = (own + 31) // 32 * 32
+    return (r + PARTS_MAX) * oss * 8 <= work_bytes
+
+
 def candidates(n_d: int, n_sm: int, refresh_k: int, runs_options: Sequence[int] = (1, 2, 3, 4),
                delay_options: Sequence[int] = (32, 64), fold_options: Sequence[int] = (1, 0),
-               own_max: int = 128, max_delay: int = 128) -> List[Candidate]:
+               own_max: int = 256, max_delay: int = 128) -> List[Candidate]:
     """Every admissible launch configuration, in a fixed order."""
     out = []
     for runs in runs_options:
@@ -71,7 +84,7 @@ def candidates(n_d: int, n_sm: int, refresh_k: int, runs_options: Sequence[int] 
         if runs < 1 or ctas < 1 or n_d > own_max * ctas:
             continue
         for r in delay_options:
-            if r < 1 or r > max_delay or (refresh_k > 0 and refresh_k % r):
+            if r < 1 or r > max_delay or (refresh_k > 0 and refresh_k % r) or not delayed_fits(n_d, ctas, r):
                 continue
             for fold in fold_options:
                 out.append(Candidate(runs, ctas, r, int(fold)))

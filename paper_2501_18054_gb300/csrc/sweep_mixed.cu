@@ -50,31 +50,38 @@ namespace {
 // spreads diag, e and the rows of T over warps of different sub-partitions.
 // FP64 appears only at set-up, after a refresh, before a fold (alpha for the
 // fold's operands) and at the end (state, trace objectives).
-constexpr int kOwnMax = 128;                                       // pixels per CTA
+constexpr int kOwnMax = 256;                                       // pixels per CTA, at most
 constexpr int kSlotStride = 16;                                    // 64-bit words between two CTAs' words
 constexpr int kSeqShift = 44;
 constexpr int kPixBits = 22;
 constexpr unsigned long long kKeyMask = (1ull << kSeqShift) - 1;
 constexpr long long kNoCand = (long long)kKeyMask;                 // above every real key
 constexpr unsigned kSeqMask = (1u << (64 - kSeqShift)) - 1;
-// FP64 own state at the start of the dynamic shared memory: T'[kMaxPorts], diag, e, dv, 1/dv, |dv|^2
-constexpr size_t kOwnStateSmem = (size_t)(kMaxPorts + 4) * kOwnMax * sizeof(c128) + kOwnMax * sizeof(double);
-constexpr size_t kXsBytes = (size_t)kMaxDelay * kOwnMax * sizeof(float2);  // delayed columns of the own pixels
-constexpr size_t kPartBytes = (size_t)16 * kOwnMax * sizeof(float2);       // U2 partial sums
+constexpr int kPartsMax = 8;                                       // warps per 32 pixels in the delayed sum
+// Own state at the start of the dynamic shared memory, one row of `oss` entries
+// each (oss = the launch's largest own-pixel count rounded up to 32): T'[n_o],
+// diag, e, dv, 1/dv (16 B), |dv|^2 (8 B); sized per launch, 1024-B aligned so
+// that the fold's operand buffers after it stay aligned.
+__host__ __device__ constexpr size_t own_state_bytes(int n_o, int oss) {
+  return (((size_t)(n_o + 4) * oss * sizeof(c128) + (size_t)oss * sizeof(double)) + 1023) / 1024 * 1024;
+}
+__host__ __device__ constexpr int own_stride(int n, int grid) { return ((n + grid - 1) / grid + 31) & ~31; }
 constexpr size_t cmax(size_t x, size_t y) { return x > y ? x : y; }
-constexpr size_t kMixedWork = cmax(cmax(kFlushSmem, kXsBytes + kPartBytes), (size_t)tc_fold_smem(2));
-static_assert(kMixedWork >= (size_t)kOwnMax * kMaxDelay * sizeof(float2), "delayed rows of the own pixels");
+// the work area: the fold's operand buffers and stage (during a fold); the
+// delayed rows of the own pixels (R x oss float2) and the delayed sum's partials
+// (kPartsMax x oss float2) between folds; the refresh's list, ring and staging
+constexpr size_t kMixedWork = cmax(kFlushSmem, (size_t)tc_fold_smem(2));
+__host__ __device__ constexpr size_t delayed_rows_bytes(int R, int oss) {
+  return ((size_t)R + kPartsMax) * oss * sizeof(float2);
+}
 static_assert(kMixedWork >= (size_t)32768 * sizeof(int), "active-pixel list of the refresh (n_d <= 32768)");
 static_assert(kMixedWork >= cs_min_smem_bytes(1 + kMaxPorts), "staging of the refresh correction");
-constexpr size_t kMixedSmem = kOwnStateSmem + kMixedWork;
-// dynamic + static (under 14 KB) shared memory stays within the 196 KB
-// carve-out, less the 1 KB a block reserves: the remaining 60 KB of L1 hold the
-// kernel's local-memory spills and its global reads
-static_assert(kMixedSmem + 14 * 1024 <= 195 * 1024, "mixed kernel shared memory");
+// dynamic + static (~17 KB) shared memory: with the own state of 108 pixels
+// (4 runs of 4096) or 216 (8 runs) and two ports, within the 196 KB carve-out,
+// which leaves 60 KB of L1 for the kernel's local-memory spills and global reads
 // a refresh holds the active list (n ints) and then the residual's copy ring
 // (its partial sums, kThreads float4, reuse the ring) in the work area
 __host__ __device__ constexpr size_t rd_list_bytes(int n) { return ((size_t)n * 4 + 15) / 16 * 16; }
-static_assert(kOwnStateSmem % 1024 == 0, "fold operands stay 1024-B aligned");
 
 // a CTA's candidate of one round, with everything the other CTAs need to keep it
 struct MixRecord {
@@ -160,13 +167,15 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   hold_if_asked(ctl);
   // own-pixel state (thread jl < own scores pixel pb + jl)
   // (double-words, so that the per-flip chain runs on the FP32 pipe; dv itself stays FP64)
-  cdd* s_T = reinterpret_cast<cdd*>(dyn_smem);  // [kMaxPorts][kOwnMax], T'_p,j = T_p,j scale_p
-  cdd* s_diag = s_T + kMaxPorts * kOwnMax;
-  cdd* s_e = s_diag + kOwnMax;
-  c128* s_dv = reinterpret_cast<c128*>(s_e + kOwnMax);
-  cdd* s_idv = reinterpret_cast<cdd*>(s_dv + kOwnMax);             // 1 / dv (0 where dv = 0)
-  dd* s_dv2 = reinterpret_cast<dd*>(s_idv + kOwnMax);                // |dv|^2
-  unsigned char* work = reinterpret_cast<unsigned char*>(dyn_smem) + kOwnStateSmem;
+  const int OSS = own_stride(n, P);  // row stride of the own state (the same in every CTA)
+  const size_t state_bytes = own_state_bytes(n_o, OSS);
+  cdd* s_T = reinterpret_cast<cdd*>(dyn_smem);  // [n_o][OSS], T'_p,j = T_p,j scale_p
+  cdd* s_diag = s_T + n_o * OSS;
+  cdd* s_e = s_diag + OSS;
+  c128* s_dv = reinterpret_cast<c128*>(s_e + OSS);
+  cdd* s_idv = reinterpret_cast<cdd*>(s_dv + OSS);             // 1 / dv (0 where dv = 0)
+  dd* s_dv2 = reinterpret_cast<dd*>(s_idv + OSS);                // |dv|^2
+  unsigned char* work = reinterpret_cast<unsigned char*>(dyn_smem) + state_bytes;
   __shared__ int s_pos[kOwnMax];
   __shared__ unsigned char s_b[kOwnMax];
   __shared__ float2 s_wk[kOwnMax];
@@ -184,9 +193,9 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
   // delayed columns of the own pixels between folds, column-major: Xs[i * OS + jl] = x_i[pb + jl]
   float2* Xs = reinterpret_cast<float2*>(work);
   // partial delayed sums of the update (U2), after the largest Xs; dead during a fold
-  float2* s_part = reinterpret_cast<float2*>(work + kXsBytes);
   const int OS = (own + 31) & ~31;
   const int R = a.R;
+  float2* s_part = reinterpret_cast<float2*>(work + (size_t)R * OSS * sizeof(float2));
   int r = ctl->r_delay;
   if (tid == 0) {
     s_op = a.op;
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     s_idv[jl] = cdd_from(cabs2(dv) > 0.0 ? cdiv(mk(1.0, 0.0), dv) : mk(0.0, 0.0));
     s_b[jl] = a.b[j];
     for (int p = 0; p < n_o; ++p)
-      s_T[p * kOwnMax + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], a.op.scale[p]));
+      s_T[p * OSS + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], a.op.scale[p]));
     if (!a.order) s_pos[jl] = j;
   }
   for (int q = tid; q < own * r; q += blockDim.x) {
@@ -228,14 +237,14 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
       const int j = pb + jl;
       a.e[j] = cdd_to(s_e[jl]);
       if (with_diag) a.diag[j] = cdd_to(s_diag[jl]);
-      for (int p = 0; p < n_o; ++p) a.T[(size_t)p * a.ldt + j] = cmul(cdd_to(s_T[p * kOwnMax + jl]), s_iscale[p]);
+      for (int p = 0; p < n_o; ++p) a.T[(size_t)p * a.ldt + j] = cmul(cdd_to(s_T[p * OSS + jl]), s_iscale[p]);
     }
   };
   auto load_et = [&]() {
     for (int jl = tid; jl < own; jl += blockDim.x) {
       const int j = pb + jl;
       s_e[jl] = cdd_from(a.e[j]);
-      for (int p = 0; p < n_o; ++p) s_T[p * kOwnMax + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], s_op.scale[p]));
+      for (int p = 0; p < n_o; ++p) s_T[p * OSS + jl] = cdd_from(cmul(a.T[(size_t)p * a.ldt + j], s_op.scale[p]));
     }
   };
   auto load_pos = [&]() {
@@ -337,11 +346,11 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           int p = 0;
 #pragma unroll 1
           for (; p + 1 < n_o; p += 2) {
-            const dd a0 = cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p]));
-            const dd a1 = cdd_abs2(cdd_fma(co, s_T[(p + 1) * kOwnMax + tid], s_S[p + 1]));
+            const dd a0 = cdd_abs2(cdd_fma(co, s_T[p * OSS + tid], s_S[p]));
+            const dd a1 = cdd_abs2(cdd_fma(co, s_T[(p + 1) * OSS + tid], s_S[p + 1]));
             fn = obj_acc<OBJ>(s_w[p + 1], a1, obj_acc<OBJ>(s_w[p], a0, fn));
           }
-          if (p < n_o) fn = obj_acc<OBJ>(s_w[p], cdd_abs2(cdd_fma(co, s_T[p * kOwnMax + tid], s_S[p])), fn);
+          if (p < n_o) fn = obj_acc<OBJ>(s_w[p], cdd_abs2(cdd_fma(co, s_T[p * OSS + tid], s_S[p])), fn);
           ok = true;
         }
       }
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         rc->b = s_b[tid];
         rc->alpha = al;
         rc->coef = co;
-        for (int p = 0; p < n_o; ++p) rc->Tk[p] = s_T[p * kOwnMax + tid];
+        for (int p = 0; p < n_o; ++p) rc->Tk[p] = s_T[p * OSS + tid];
       };
       if (a.mode == PNGF_FIRST_IMPROVEMENT) {
         long long cand = kNoCand;
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
     // `parts` warps per block, whose partial sums meet in shared memory.
     {
       const int nb = (own + 31) >> 5;
-      const int parts = nb <= 2 ? 8 : 4;
+      const int parts = min(kPartsMax, (kThreads / 32) / nb);  // nb * parts <= the CTA's warps
       if (warp < nb * parts) {
         const int jl = (warp % nb) * 32 + lane, part = warp / nb;
         float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
@@ -553,7 +562,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
             ax = fmaf(b0.x, x0.x, fmaf(-b0.y, x0.y, ax));
             ay = fmaf(b0.x, x0.y, fmaf(b0.y, x0.x, ay));
           }
-          s_part[part * kOwnMax + jl] = make_float2(ax + bx, ay + by);
+          s_part[part * OSS + jl] = make_float2(ax + bx, ay + by);
         }
       }
       __syncthreads();
@@ -563,8 +572,8 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         const int jl = tid;
         float sx = s_wk[jl].x, sy = s_wk[jl].y, dx = 0.f, dy = 0.f;
         for (int q = 0; q < parts; ++q) {
-          dx += s_part[q * kOwnMax + jl].x;
-          dy += s_part[q * kOwnMax + jl].y;
+          dx += s_part[q * OSS + jl].x;
+          dy += s_part[q * OSS + jl].y;
         }
         const float2 cf = make_float2(sx + dx, sy + dy);
         s_c[jl] = cf;
@@ -593,7 +602,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           } else if (q == 1) {
             s_e[jl] = cdd_add(s_e[jl], cdd_mul_cf(s_pv.coef, s_c[jl].x, s_c[jl].y));
           } else {
-            cdd* tq = s_T + (q - 2) * kOwnMax + jl;
+            cdd* tq = s_T + (q - 2) * OSS + jl;
             *tq = cdd_fma(s_ac[jl], s_pv.Tk[q - 2], *tq);
           }
         }
@@ -631,7 +640,7 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         }
         tick(9);
         correct_strips<true>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(work),
-                             (int)(dynamic_smem_bytes() - kOwnStateSmem));
+                             (int)(dynamic_smem_bytes() - state_bytes));
         if (!grid_sync(ctl)) { failed = true; break; }
         tick(10);
         ports_partial(a, pb, pe);
@@ -780,24 +789,30 @@ static void* mixed_kernel_for(int objective) {
                                                   : (void*)dbs_mixed_kernel<PNGF_OBJ_MIN_INSERTION_LOSS>;
 }
 
+// dynamic shared memory of a launch: the own state of its largest CTA share, then the work area
+static size_t mixed_smem(const pngf_ctx* c, int grid) {
+  return own_state_bytes(c->cfg.n_o, own_stride(c->cfg.n_d, grid)) + kMixedWork;
+}
+
 static int mixed_grid(pngf_ctx* c) {
   static bool attr = false;
-  if (!attr) {
+  if (!attr) {  // room for the largest own state (8 ports, kOwnMax pixels per CTA)
+    const int most = (int)(own_state_bytes(kMaxPorts, kOwnMax) + kMixedWork);
     cudaFuncSetAttribute(dbs_mixed_kernel<PNGF_OBJ_MAX_WEIGHTED_POWER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kMixedSmem);
+                         most);
     cudaFuncSetAttribute(dbs_mixed_kernel<PNGF_OBJ_MIN_INSERTION_LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kMixedSmem);
+                         most);
     cudaFuncSetAttribute(flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFlushSmem);
     attr = true;
   }
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel_for(c->cfg.objective), kThreads, kMixedSmem);
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
-  int g = c->n_sm * per_sm;
+  // one CTA per SM: the work area alone is more than half of an SM's shared memory
+  int g = c->n_sm;
   if (c->cfg.n_ctas > 0 && c->cfg.n_ctas < g) g = c->cfg.n_ctas;
   if (g > c->L.n_part) g = c->L.n_part;
-  return g;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel_for(c->cfg.objective), kThreads,
+                                                mixed_smem(c, g));
+  return per_sm >= 1 ? g : 0;
 }
 
 pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int32_t* trace, double* trace_f,
@@ -811,7 +826,10 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   a.counters = counters;
   Control* ctl = a.ctl;
   int grid = mixed_grid(c);
+  if (grid < 1) return PNGF_EINVAL;  // the own state does not fit in shared memory
   if ((c->cfg.n_d + grid - 1) / grid > kOwnMax) return PNGF_EINVAL;  // own-pixel state is shared memory
+  // the delayed rows of the own pixels and the delayed sum's partials fit in the work area
+  if (delayed_rows_bytes(a.R, own_stride(c->cfg.n_d, grid)) > kMixedWork) return PNGF_EINVAL;
   {  // the refresh residual's copy ring takes one list entry per group and stage at least, after the active list
     const int own = (c->cfg.n_d + grid - 1) / grid;
     const size_t list = rd_list_bytes(c->cfg.n_d);
@@ -824,8 +842,8 @@ pngf_status run_sweep_mixed(pngf_ctx* c, int n_sweeps, const int32_t* order, int
   err = cudaMemsetAsync(a.slots, 0, (size_t)2 * grid * kSlotStride * sizeof(unsigned long long), c->stream);
   if (err != cudaSuccess) return PNGF_ECUDA;
   void* params[] = {&a};
-  err = cudaLaunchCooperativeKernel(mixed_kernel_for(c->cfg.objective), dim3(grid), dim3(kThreads), params, kMixedSmem,
-                                    c->stream);
+  err = cudaLaunchCooperativeKernel(mixed_kernel_for(c->cfg.objective), dim3(grid), dim3(kThreads), params,
+                                    mixed_smem(c, grid), c->stream);
   return cuda_status(err);
 }
 

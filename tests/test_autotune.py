@@ -7,11 +7,14 @@ from paper_2501_18054_gb300 import autotune as A
 def test_candidates_respect_capacity_and_refresh():
     c = A.candidates(4096, 152, 64)
     assert c and all(x.ctas == 152 // x.runs for x in c)
-    assert all(4096 <= 128 * x.ctas for x in c)  # 4096 pixels need >= 32 CTAs per run
+    assert all(4096 <= 256 * x.ctas for x in c)  # at most 256 pixels per CTA
     assert {x.runs for x in c} == {1, 2, 3, 4}
     assert all(64 % x.delay_r == 0 for x in c)
-    # five runs would give 30 CTAs per run: 137 pixels per CTA, above the shared-memory share
-    assert not [x for x in A.candidates(4096, 152, 64, runs_options=(5,))]
+    # eight runs: 19 CTAs of 216 pixels (224 rounded); R = 64 leaves (64 + 8) x 224 x 8 = 129 KB
+    eight = A.candidates(4096, 152, 64, runs_options=(8,), delay_options=(64, 128))
+    assert {x.delay_r for x in eight} == {64}  # R = 128 would need 243 KB
+    # ten runs: 15 CTAs of 274 pixels, above 256 per CTA
+    assert not A.candidates(4096, 152, 64, runs_options=(10,))
     assert not A.candidates(4096, 152, 48, delay_options=(32,))  # 48 is not a multiple of 32
     assert len(A.candidates(100, 152, 64, runs_options=(1, 2, 4, 8), delay_options=(16, 32, 64))) == 4 * 3 * 2
 

@@ -249,12 +249,18 @@ def test_tensor_fold_matches_cuda_core_fold(P, name, delay_r, n_acc):
 
 
 def test_mixed_sweep_rejects_grid_too_small(P, fdfd64):
-    """More than 128 pixels per CTA of the persistent grid is refused before any launch."""
+    """More than 256 pixels per CTA of the persistent grid, or more delayed rows
+    than the work area holds, is refused before any launch."""
     ctx = _ctx(P, fdfd64, delay_r=8, refresh_k=16, n_ctas=1)  # 100 pixels on one CTA: accepted
     ctx.factor(W.random_design(fdfd64.n_d, 0))
     ctx.dbs_sweep(1)
     big = W.get_case("fdfd128_metal")  # 1024 pixels
-    ctx = _ctx(P, big, delay_r=8, refresh_k=16, n_ctas=4)  # 256 per CTA
+    ctx = _ctx(P, big, delay_r=8, refresh_k=16, n_ctas=3)  # 342 per CTA
+    ctx.factor(W.random_design(big.n_d, 0))
+    with pytest.raises(P.PngfError) as ei:
+        ctx.dbs_sweep(1)
+    assert ei.value.status == P.PNGF_EINVAL
+    ctx = _ctx(P, big, delay_r=128, refresh_k=128, n_ctas=4)  # 256 per CTA x (128 + 8) delayed rows: 272 KB
     ctx.factor(W.random_design(big.n_d, 0))
     with pytest.raises(P.PngfError) as ei:
         ctx.dbs_sweep(1)
