@@ -38,8 +38,8 @@ WORKLOAD = "fdfd256_nd4096"  # 256^2 FDFD, 16-cell PML, eps=2.2 slab, 64x64 desi
 # that launch.  A step's traffic is this ratio times the step's algorithmic bytes, reported only
 # while the kernel code is the captured one (fingerprint of the sources without comments), else null.
 TRAFFIC_CAPTURE = {"kernel": "dbs_mixed_kernel", "workload": "fdfd256_nd4096",
-                   "measured_bytes": 2.852148e9 + 1.078067e9, "algorithmic_bytes": 4509239696.0,
-                   "sources_sha256": "d798c8cd37d60357a0039c84762f14820dd4092246e434629e9c561a13c69003"}
+                   "measured_bytes": 2.643335e9 + 0.982979e9, "algorithmic_bytes": 4509239696.0,
+                   "sources_sha256": "e8b3e4de3c92094e911ea4e935a84af77b08b73ae56a4b4a3296b248cd83c7c4"}
 
 
 def _code_only(src: str) -> str:
@@ -105,6 +105,8 @@ def parse():
     ap.add_argument("--cpu-sample-evals", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ctas-per-run", type=int, default=0,
+                    help="CTAs of each run's cooperative launch (0: the SMs divided among the runs)")
     ap.add_argument("--hankel-sweeps", type=int, default=2,
                     help="hankel128_nd16384: sweeps per run (the third drives the lossless design into a "
                          "high-Q resonance where the FP32 inverse of the mixed path stops with PNGF_EACCURACY)")
@@ -800,7 +802,7 @@ def main():
                  "note": "successive halving over runs per GPU x delay R x fold engine; every trial's final "
                          "designs equal the FP64 path's and S within 1e-4"}
     n_runs = max(1, args.runs)
-    ctas = 0 if n_runs == 1 else nsm // n_runs
+    ctas = args.ctas_per_run if args.ctas_per_run > 0 else (0 if n_runs == 1 else nsm // n_runs)
     seeds = [dist.rank * n_runs + i for i in range(n_runs)]
     rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream)
     for _ in range(max(args.warmup, 1)):
@@ -880,8 +882,9 @@ def main():
         if args.workload == TRAFFIC_CAPTURE["workload"] and sources_fingerprint() == TRAFFIC_CAPTURE["sources_sha256"]:
             ratio = TRAFFIC_CAPTURE["measured_bytes"] / TRAFFIC_CAPTURE["algorithmic_bytes"]
             traffic = ratio * bytes_alg
-            traffic_note = ("bytes per step: ncu dram read + write of one captured launch (one run, seed 0) "
-                            "= %.3f x its algorithmic bytes, scaled to this step's algorithmic bytes" % ratio)
+            traffic_note = ("bytes per step: ncu dram read + write of one captured launch (one run, seed 0, "
+                            "19 CTAs: the headline launch shape) = %.3f x its algorithmic bytes, scaled to "
+                            "this step's algorithmic bytes" % ratio)
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                     "traffic": traffic, "traffic_note": traffic_note, "algorithmic_bytes_per_step": bytes_alg,
                     "kernel": "dbs_mixed_kernel",
