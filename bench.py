@@ -153,6 +153,11 @@ class Dist:
         return float(t.item())
 
 
+def replica_seeds(rank: int, runs: int) -> list:
+    """Seeds of one rank's independent runs: disjoint across ranks (rank * runs + i)."""
+    return [rank * runs + i for i in range(runs)]
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -803,7 +808,7 @@ def main():
                          "designs equal the FP64 path's and S within 1e-4"}
     n_runs = max(1, args.runs)
     ctas = args.ctas_per_run if args.ctas_per_run > 0 else (0 if n_runs == 1 else nsm // n_runs)
-    seeds = [dist.rank * n_runs + i for i in range(n_runs)]
+    seeds = replica_seeds(dist.rank, n_runs)
     rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream)
     for _ in range(max(args.warmup, 1)):
         rs.step()
