@@ -104,6 +104,10 @@ def parse():
     ap.add_argument("--tau", type=float, default=1e-9)
     ap.add_argument("--cpu-sample-evals", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-one-core", action="store_true",
+                    help="also time the oracle with one BLAS thread (two solves, ~1 min at N_d = 4096)")
+    ap.add_argument("--cpu-kept-flips", type=int, default=24,
+                    help="kept flips of the numpy Sherman-Morrison baseline's sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ctas-per-run", type=int, default=0,
                     help="CTAs of each run's cooperative launch (0: the SMs divided among the runs)")
@@ -228,6 +232,86 @@ def time_oracle(case, b0, n_evals: int):
     res = O.dbs(p, b0, np.arange(case.n_d, dtype=np.int32)[None, :], tau=1e-9, max_evals=n_evals)
     dt = time.perf_counter() - t0
     return res.n_evals / dt, res.n_evals, dt
+
+
+def time_paper_algorithm(case, b0, n_kept: int, sweeps: int = 10):
+    """The paper's own CPU algorithm written plainly with numpy and the threaded
+    BLAS (the counterpart of Table 1's "PNGF on BLAS/LAPACK"): factor once
+    (LAPACK solve for W = M^-1 G and e, T = G_od (I + V W)), then first-improvement
+    DBS in raster order where every candidate is scored in O(n_o) (Eq. 14, field
+    form) and a kept flip updates W, T, e by rank 1 (Eq. 9, BLAS zgeru in place).
+    Returns (evals/s, evaluations, kept flips, seconds of search, seconds of factor)
+    over the first ``n_kept`` kept flips of the run."""
+    import scipy.linalg as sla
+    from scipy.linalg import blas
+    n, G = case.n_d, case.G_dd
+    dv, s_off, s_scale, w = case.dv, case.s_off, case.s_scale, case.obj_weights
+    kind = int(case.obj_kind)
+
+    def fobj(o):  # o: (n_o, m) port amplitudes -> objective per column
+        a = np.abs((o - s_off[:, None]) * s_scale[:, None])
+        return np.sum(w[:, None] * (a * a if kind == 0 else (1.0 - a) ** 2), axis=0)
+
+    b = np.asarray(b0, dtype=np.uint8).copy()
+    t0 = time.perf_counter()
+    v = dv * b
+    sol = sla.solve(np.eye(n, dtype=np.complex128) - G * v[None, :], np.concatenate([G, case.c_d[:, None]], 1))
+    W = np.ascontiguousarray(sol[:, :n])
+    e = sol[:, n].copy()
+    T = case.G_od + (case.G_od * v[None, :]) @ W
+    o = case.c_o + case.G_od @ (v * e)
+    t_factor = time.perf_counter() - t0
+    f = float(fobj(o[:, None])[0])
+    evals = kept = 0
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        t, kept_in_sweep = 0, 0
+        while t < n and kept < n_kept:
+            delta = np.where(b[t:] == 1, -dv[t:], dv[t:])
+            d = 1.0 - delta * np.diagonal(W)[t:]
+            alpha = delta / d
+            coef = alpha * e[t:]
+            fn = fobj(o[:, None] + coef[None, :] * T[:, t:])
+            gain = fn - f if kind == 0 else f - fn
+            hit = np.flatnonzero(gain > 1e-9 * max(abs(f), 1e-30))
+            if len(hit) == 0:
+                evals += n - t
+                t = n
+                break
+            q = int(hit[0])
+            k = t + q
+            evals += q + 1
+            c = W[:, k].copy()
+            Tk = T[:, k].copy()
+            blas.zgeru(alpha[q], c, c, a=W.T, overwrite_a=1)  # W += alpha c c^T (W symmetric)
+            T += alpha[q] * np.outer(Tk, c)
+            e += coef[q] * c
+            o = o + coef[q] * Tk
+            f = float(fn[q])
+            b[k] ^= 1
+            kept += 1
+            kept_in_sweep += 1
+            t = k + 1
+        if kept >= n_kept or kept_in_sweep == 0:
+            break
+    dt = time.perf_counter() - t0
+    return evals / dt, evals, kept, dt, t_factor
+
+
+def time_oracle_one_core(workload: str, n_evals: int):
+    """The oracle timed in a child process limited to one BLAS thread."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, numpy as np; "
+            "from paper_2501_18054_gb300 import workloads as Wl; "
+            "c = Wl.get_case(bench.case_name(%r)); "
+            "print(json.dumps(bench.time_oracle(c, Wl.random_design(c.n_d, 0), %d)))" % (ROOT, workload, n_evals))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        v, m, dt = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"first {m} attempted flips re-solved with one BLAS thread ({dt:.1f} s)"}
+    except Exception as ex:  # a baseline, not the measurement: report why it is missing
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[:200]}
 
 
 def blas_threads() -> int:
@@ -998,6 +1082,13 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                "sample": f"first {m} attempted flips of the same raster DBS run, each re-solved with "
                          f"LAPACK zgesv at n={n} ({dt:.1f} s)"}
+        if args.cpu_one_core:
+            cpu["one_core"] = time_oracle_one_core(args.workload, 1)
+        pv, pe, pk, pdt, pfac = time_paper_algorithm(case, Wl.random_design(n, seed=seeds[0]), args.cpu_kept_flips)
+        cpu["paper_algorithm"] = {"value": pv, "unit": UNIT, "cores": blas_threads(),
+                                  "kind": "the paper's Sherman-Morrison DBS in numpy + threaded BLAS",
+                                  "sample": f"first {pk} kept flips ({pe} attempted) of the same run, "
+                                            f"{pdt:.1f} s; its factor {pfac:.1f} s (not counted)"}
     if dist.rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=dist.world, steps=args.steps, warmup=args.warmup,
