@@ -106,7 +106,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-one-core", action="store_true",
                     help="also time the oracle with one BLAS thread (two solves, ~1 min at N_d = 4096)")
-    ap.add_argument("--cpu-kept-flips", type=int, default=24,
+    ap.add_argument("--cpu-kept-flips", type=int, default=300,
                     help="kept flips of the numpy Sherman-Morrison baseline's sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ctas-per-run", type=int, default=0,
