@@ -145,7 +145,7 @@ __device__ void refresh_x_df(const SweepArgs& a, int pb, int pe, const int* act,
 //
 // area, area_bytes: 16-byte aligned shared memory for the ring (the partial
 // sums reuse it: blockDim float4).
-constexpr int RD_D = 4;
+constexpr int RD_D = 3;
 constexpr float kRefreshGuard = 1e-3f;  // largest relative residual of e the mixed search accepts
 constexpr int RD_RMAX = 8;
 // list entries per group and stage for own rows and NV vectors in area_bytes (0: too small)
