@@ -97,7 +97,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--runs", type=int, default=4,
-                    help="independent runs per GPU (random starts), launched side by side on their own streams")
+                    help="independent runs side by side on their own streams (concurrent slots)")
+    ap.add_argument("--runs-per-slot", type=int, default=4,
+                    help="mixed/FP64 headline: runs queued one after another on each slot's stream; a step "
+                         "is runs x runs-per-slot independent searches")
     # kept flips between refreshes of the mixed path (a multiple of --delay-r); the headline
     # configuration refreshes every 64 kept flips
     ap.add_argument("--refresh-k", type=int, default=64)
@@ -721,17 +724,21 @@ def bench_side(args, torch, dist, dev, P, Wl):
 
 # ---------------------------------------------------------------- GPU arm
 class RunSet:
-    """B independent DBS runs (seeds seed0 .. seed0 + B - 1) on one device, each
-    with its own context, stream and persistent grid of ctas CTAs; a step forks
-    from the timing stream, runs restore + pngf_dbs_sweep on every run's stream
-    (the cooperative launches execute side by side) and joins back."""
+    """B independent DBS runs (seeds) on one device, each with its own context
+    and persistent grid of ctas CTAs, dealt round-robin onto `slots` streams
+    (default: one stream per run); a step forks from the timing stream, runs
+    restore + pngf_dbs_sweep of every run on its slot's stream (the slots'
+    cooperative launches execute side by side, a slot's runs one after another)
+    and joins back."""
 
-    def __init__(self, torch, P, Wl, case, dev, precision, args, seeds, ctas, tstream, inputs=None):
+    def __init__(self, torch, P, Wl, case, dev, precision, args, seeds, ctas, tstream, inputs=None, slots=None):
         self.torch, self.P, self.case, self.dev, self.tstream = torch, P, case, dev, tstream
         self.n = case.n_d
         self.sweeps = args.sweeps
         self.trace_cap = args.sweeps * self.n
-        self.streams = [torch.cuda.Stream(dev) for _ in seeds]
+        self.slots = len(seeds) if slots is None else max(1, min(slots, len(seeds)))
+        self.slot_streams = [torch.cuda.Stream(dev) for _ in range(self.slots)]
+        self.streams = [self.slot_streams[i % self.slots] for i in range(len(seeds))]  # per run
         self.ctxs, self.traces, self.trace_f, self.counters = [], [], [], []
         self.factor_ms = []
         for i, seed in enumerate(seeds):
@@ -766,11 +773,11 @@ class RunSet:
         torch, P = self.torch, self.P
         fork = torch.cuda.Event()
         fork.record(self.tstream)
-        joins = []
+        for s in self.slot_streams:
+            s.wait_event(fork)
         for r, (c, s) in enumerate(zip(self.ctxs, self.streams)):
             if subset is not None and r not in subset:
                 continue
-            s.wait_event(fork)
             P.pngf_restore(c.ctx)
             if i_step is not None:
                 self.kev[i_step][r][0].record(s)
@@ -778,10 +785,9 @@ class RunSet:
                              self.trace_f[r].data_ptr(), self.trace_cap, self.counters[r].data_ptr())
             if i_step is not None:
                 self.kev[i_step][r][1].record(s)
+        for s in self.slot_streams:
             j = torch.cuda.Event()
             j.record(s)
-            joins.append(j)
-        for j in joins:
             self.tstream.wait_event(j)
 
     def arm_events(self, steps):
@@ -890,10 +896,12 @@ def main():
                  "trials": [t.as_dict() for t in trials],
                  "note": "successive halving over runs per GPU x delay R x fold engine; every trial's final "
                          "designs equal the FP64 path's and S within 1e-4"}
-    n_runs = max(1, args.runs)
-    ctas = args.ctas_per_run if args.ctas_per_run > 0 else (0 if n_runs == 1 else nsm // n_runs)
+    n_slots = max(1, args.runs)  # concurrent runs
+    per_slot = max(1, args.runs_per_slot)
+    n_runs = n_slots * per_slot  # runs per step
+    ctas = args.ctas_per_run if args.ctas_per_run > 0 else (0 if n_slots == 1 else nsm // n_slots)
     seeds = replica_seeds(dist.rank, n_runs)
-    rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream)
+    rs = RunSet(torch, P, Wl, case, dev, prec, args, seeds, ctas, tstream, slots=n_slots)
     for _ in range(max(args.warmup, 1)):
         rs.step()
     torch.cuda.synchronize(dev)
@@ -940,8 +948,9 @@ def main():
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     tri = n * (n + 1) / 2
-    runs_note = ("%d concurrent cooperative launches (one per run, %d CTAs each): achieved = the launches' "
-                 "algorithmic work per step / device time of a step" % (n_runs, ctas)) if n_runs > 1 else None
+    runs_note = ("%d runs per step, %d at a time (%d streams of %d cooperative launches one after another, "
+                 "%d CTAs each): achieved = the launches' algorithmic work per step / device time of a step"
+                 % (n_runs, n_slots, n_slots, per_slot, ctas or nsm)) if n_runs > 1 else None
     if prec == P.PNGF_FP64:
         # dominant kernel: the persistent FP64 DBS sweep.  Algorithmic work per
         # launch: the rank-1 update of the upper triangle of W per kept flip,
@@ -1027,7 +1036,8 @@ def main():
                 for r, cx in enumerate(rs.ctxs)]
     compare = None
     if prec == P.PNGF_MIXED and not args.no_fp64_compare:
-        ref = RunSet(torch, P, Wl, case, dev, P.PNGF_FP64, args, seeds, ctas, tstream, inputs=rs.inputs)
+        ref = RunSet(torch, P, Wl, case, dev, P.PNGF_FP64, args, seeds, ctas, tstream, inputs=rs.inputs,
+                     slots=n_slots)
         ref.step()
         torch.cuda.synchronize(dev)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1095,7 +1105,8 @@ def main():
             ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f64" if prec == P.PNGF_FP64 else "f32+f64", data="synthetic",
             config={"workload": args.workload, "n_d": n, "n_o": n_o, "precision": args.precision,
-                    "runs_per_gpu": n_runs, "ctas_per_run": ctas if ctas else nsm,
+                    "runs_per_gpu": n_runs, "concurrent_runs": n_slots, "runs_per_slot": per_slot,
+                    "ctas_per_run": ctas if ctas else nsm,
                     "seeds": seeds,
                     "mode": "first-improvement, raster order", "max_sweeps": args.sweeps,
                     "refresh_k": args.refresh_k, "tau": args.tau,
@@ -1103,7 +1114,8 @@ def main():
                     "fold": ("tcgen05 3xTF32" if args.tensor_fold else "FP32 CUDA cores")
                     if prec == P.PNGF_MIXED else None,
                     "step": "restore every run's factored start state + DBS for up to %d sweeps or until "
-                            "a sweep keeps no flip, runs concurrent" % args.sweeps,
+                            "a sweep keeps no flip; %d runs at a time, %d after one another on each of %d "
+                            "streams" % (args.sweeps, n_slots, per_slot, n_slots),
                     "l2": "inputs larger than L2 (W = %.0f MB complex128 per run)" % (n * n * 16 / 1e6),
                     "replicas": "independent runs per GPU (seed = rank * runs + i)"},
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk, gpu_launches=args.steps * n_runs,

@@ -282,5 +282,226 @@ __device__ void refresh_residual_df(const SweepArgs& a, int pb, int pe, const in
   }
 }
 
+// ---------------------------------------------------------------- FP32 correction, balanced (mixed search)
+// y = W x2 for every row (W symmetric, its upper triangle current in the FP32
+// planes, x2 = v.r), with the triangle's work dealt evenly over the grid
+// instead of by own rows (own rows near the top of the triangle carry the
+// longest rows, so the CTA holding them set the pace of the whole refresh):
+//  - upper part sum_{i>=j} W[j][i] x2_i, row by row in groups of 2 nw rows: a
+//    warp takes rows j and j + nw, which share every staged x2 read, lanes read
+//    four-wide along the rows;
+//  - lower part sum_{i<j} W[i][j] x2_i, column by column in blocks of 32
+//    (lane = column), over the active rows i < j only (x2 vanishes elsewhere).
+// Round k of the groups (of the blocks) gives CTA c item k G + c for even k and
+// k G + G - 1 - c for odd k: the snake pairs long rows with short ones and
+// tall column blocks with low ones.  Upper sums go to block 3 of the scratch,
+// lower sums to block 1; correct_combine adds r + upper + lower into e and T of
+// the own rows once a grid barrier has made them visible.
+// act: the ascending active-pixel list (global memory), m its length; smem:
+// smem_bytes of shared memory (16-byte aligned).
+__device__ __forceinline__ int snake_item(int k, int c, int G) { return k * G + ((k & 1) ? G - 1 - c : c); }
+
+template <int NV>
+__device__ __noinline__ void correct_balanced_t(const SweepArgs& a, const int* act, int m, float* smem, int smem_bytes) {
+  const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)blockDim.x >> 5;
+  const int G = (int)gridDim.x, cta = (int)blockIdx.x;
+  float2* red = reinterpret_cast<float2*>(smem);  // [warps][NV][32]
+  float2* xs = red + nw * NV * 32;
+  const int avail = smem_bytes - nw * NV * 32 * (int)sizeof(float2);
+  // ---- upper part
+  const int n128 = (n + 127) & ~127;
+  const int cw = min(n128, avail / (NV * (int)sizeof(float2)) / 128 * 128);
+  const bool whole = cw >= n128;  // x2 staged once for every group
+  const int RG = 2 * nw, n_groups = (n + RG - 1) / RG;
+  bool staged = false;
+  for (int k = 0; k * G < n_groups; ++k) {
+    const int g = snake_item(k, cta, G);
+    if (g >= n_groups) continue;
+    const int g0 = g * RG, j1 = g0 + warp, j2 = g0 + warp + nw;
+    f2c acc1[NV], acc2[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc1[q] = acc2[q] = f2c{0.f, 0.f};
+    const int cstart = whole ? 0 : (g0 & ~127);
+    for (int c0 = cstart; c0 < n; c0 += cw) {
+      if (!whole || !staged) {
+        __syncthreads();
+        // column cc of the chunk at (cc & 3) * (cw / 4) + (cc >> 2): lanes read consecutive words;
+        // four reads in flight per thread before their stores
+        for (int e0 = tid; e0 < NV * cw; e0 += 4 * blockDim.x) {
+          float2 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x, q = e / cw, cc = e - q * cw, col = c0 + cc;
+            v[u] = e < NV * cw && col < n ? x2f(a, q)[col] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x, q = e / cw, cc = e - q * cw;
+            if (e < NV * cw) xs[q * cw + (cc & 3) * (cw >> 2) + (cc >> 2)] = v[u];
+          }
+        }
+        __syncthreads();
+        staged = true;
+      }
+      if (j1 < n) {
+        const int kb = max(0, ((j1 & ~3) - c0) >> 7), ke = min(cw, n - c0 + 127) >> 7;
+        for (int k0 = kb; k0 < ke; k0 += 4) {  // four four-wide reads of each row in flight per lane
+          f2c w1[4][4], w2[4][4];
+#pragma unroll
+          for (int u4 = 0; u4 < 4; ++u4) {
+            const int col = c0 + 128 * (k0 + u4) + 4 * lane;
+            const bool in = k0 + u4 < ke && col < n;
+            if (in && col + 3 >= j1) {
+              w_row4<true>(a, j1, col, w1[u4]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) w1[u4][u] = f2c{0.f, 0.f};
+            }
+            if (in && j2 < n && col + 3 >= j2) {
+              w_row4<true>(a, j2, col, w2[u4]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) w2[u4][u] = f2c{0.f, 0.f};
+            }
+          }
+#pragma unroll
+          for (int u4 = 0; u4 < 4; ++u4) {
+            const int kk = k0 + u4;
+            if (kk < ke) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int i = c0 + 128 * kk + 4 * lane + u;
+                const bool ok1 = i >= j1 && i < n, ok2 = i >= j2 && i < n;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                  const float2 x = xs[q * cw + u * (cw >> 2) + 32 * kk + lane];
+                  if (ok1) acc1[q] = f2fma(w1[u4][u], f2c{x.x, x.y}, acc1[q]);
+                  if (ok2) acc2[q] = f2fma(w2[u4][u], f2c{x.x, x.y}, acc2[q]);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const f2c s1 = f2sum(acc1[q]), s2 = f2sum(acc2[q]);
+      if (lane == 0 && j1 < n) rvec(a, 3, q)[j1] = mk(s1.x, s1.y);
+      if (lane == 0 && j2 < n) rvec(a, 3, q)[j2] = mk(s2.x, s2.y);
+    }
+  }
+  // ---- lower part: blocks of 32 columns, rows from the staged active list
+  const int rcap = max(1, min(max(m, 1), avail / (int)(sizeof(int) + NV * sizeof(float2))));
+  int* rows = reinterpret_cast<int*>(xs + NV * rcap);
+  const bool fits = m <= rcap;  // every active row staged once
+  if (fits) {
+    __syncthreads();
+    for (int e = tid; e < m; e += blockDim.x) rows[e] = act[e];
+    __syncthreads();
+    for (int e0 = tid; e0 < NV * m; e0 += 4 * blockDim.x) {  // four reads in flight per thread
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x, q = e / m, tt = e - q * m;
+        v[u] = e < NV * m ? x2f(a, q)[rows[tt]] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x, q = e / m, tt = e - q * m;
+        if (e < NV * m) xs[q * rcap + tt] = v[u];
+      }
+    }
+    __syncthreads();
+  }
+  const int n_blocks = (n + 31) / 32;
+  for (int k = 0; k * G < n_blocks; ++k) {
+    const int bi = snake_item(k, cta, G);
+    if (bi >= n_blocks) continue;
+    const int cb = bi * 32, j = cb + lane;
+    const bool colok = j < n;
+    // active rows above the block's last column (searched in the staged copy when it holds them all)
+    const int t_blk = count_below(fits ? rows : act, m, min(cb + 31, n - 1));
+    f2c acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = f2c{0.f, 0.f};
+    for (int t0 = 0; t0 < t_blk; t0 += rcap) {
+      const int cnt = min(rcap, t_blk - t0);
+      if (!fits) {
+        __syncthreads();
+        for (int e = tid; e < cnt; e += blockDim.x) rows[e] = act[t0 + e];
+        __syncthreads();
+        for (int e = tid; e < NV * cnt; e += blockDim.x) {
+          const int q = e / cnt, tt = e - q * cnt;
+          xs[q * rcap + tt] = x2f(a, q)[rows[tt]];
+        }
+        __syncthreads();
+      }
+      for (int tt = warp; tt < cnt; tt += CS_UNROLL * nw) {
+        f2c w[CS_UNROLL];
+#pragma unroll
+        for (int u = 0; u < CS_UNROLL; ++u) {
+          const int t2 = tt + u * nw;
+          w[u] = f2c{0.f, 0.f};
+          if (t2 < cnt) {
+            const int i = rows[t2];
+            if (colok && i < j) w[u] = w_upper<true>(a, i, j);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < CS_UNROLL; ++u) {
+          const int t2 = tt + u * nw;
+          if (t2 < cnt) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const float2 x = xs[q * rcap + t2];
+              acc[q] = f2fma(w[u], f2c{x.x, x.y}, acc[q]);
+            }
+          }
+        }
+      }
+    }
+    // the warps' column partials, summed in warp order
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[(warp * NV + q) * 32 + lane] = make_float2(acc[q].x, acc[q].y);
+    __syncthreads();
+    if (warp < NV && colok) {
+      const int q = warp;
+      float sx = 0.f, sy = 0.f;
+      for (int w2 = 0; w2 < nw; ++w2) {
+        sx += red[(w2 * NV + q) * 32 + lane].x;
+        sy += red[(w2 * NV + q) * 32 + lane].y;
+      }
+      rvec(a, 1, q)[j] = mk((double)sx, (double)sy);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void correct_balanced(const SweepArgs& a, const int* act, int m, float* smem, int smem_bytes) {
+  switch (a.n_o) {
+    case 1: correct_balanced_t<2>(a, act, m, smem, smem_bytes); break;
+    case 2: correct_balanced_t<3>(a, act, m, smem, smem_bytes); break;
+    case 3: correct_balanced_t<4>(a, act, m, smem, smem_bytes); break;
+    case 4: correct_balanced_t<5>(a, act, m, smem, smem_bytes); break;
+    case 5: correct_balanced_t<6>(a, act, m, smem, smem_bytes); break;
+    case 6: correct_balanced_t<7>(a, act, m, smem, smem_bytes); break;
+    case 7: correct_balanced_t<8>(a, act, m, smem, smem_bytes); break;
+    default: correct_balanced_t<9>(a, act, m, smem, smem_bytes); break;
+  }
+}
+
+// e, T of the own rows += r + upper + lower (after the grid barrier that
+// follows correct_balanced)
+__device__ void correct_combine(const SweepArgs& a, int pb, int pe) {
+  const int own = pe - pb, nv = 1 + a.n_o;
+  for (int e = threadIdx.x; e < nv * own; e += blockDim.x) {
+    const int q = e / own, j = pb + (e - q * own);
+    const c128 d = cadd(rvec(a, 0, q)[j], cadd(rvec(a, 3, q)[j], rvec(a, 1, q)[j]));
+    c128* dst = q == 0 ? a.e + j : a.T + (size_t)(q - 1) * a.ldt + j;
+    *dst = cadd(*dst, d);
+  }
+}
+
 }  // namespace
 }  // namespace pngf

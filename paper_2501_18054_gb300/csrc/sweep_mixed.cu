@@ -631,7 +631,6 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
         tick(8);
         // the residual's copy ring after the list
         refresh_residual_df(a, pb, pe, act, m_act, work + rd_list_bytes(n), (unsigned)(kMixedWork - rd_list_bytes(n)));
-        const int t_end = count_below(act, m_act, pe - 1);
         if (!grid_sync(ctl)) { failed = true; break; }
         // the accuracy guard of any CTA ends the search in every CTA (read after the barrier)
         if (*reinterpret_cast<volatile int*>(&ctl->status) == PNGF_EACCURACY) {
@@ -639,9 +638,10 @@ __global__ void __launch_bounds__(kThreads) dbs_mixed_kernel(SweepArgs a) {
           break;
         }
         tick(9);
-        correct_strips<true>(a, pb, pe, a.actg, t_end, reinterpret_cast<float*>(work),
-                             (int)(dynamic_smem_bytes() - state_bytes));
+        correct_balanced(a, a.actg, m_act, reinterpret_cast<float*>(work), (int)(dynamic_smem_bytes() - state_bytes));
         if (!grid_sync(ctl)) { failed = true; break; }
+        correct_combine(a, pb, pe);
+        __syncthreads();
         tick(10);
         ports_partial(a, pb, pe);
         if (!grid_sync(ctl)) { failed = true; break; }

@@ -97,6 +97,35 @@ def test_mixed_refresh_restores_fp64_accuracy(P, fdfd64, tensor_fold):
     assert errs[0] > 100 * errs[16]
 
 
+@pytest.fixture(scope="module")
+def fdfd256():
+    return W.get_case("fdfd256")
+
+
+@pytest.mark.parametrize("n_sub,n_ctas", [(997, 5), (1024, 7), (1501, 19), (4096, 19)])
+def test_mixed_refresh_accuracy_across_grids(P, fdfd256, n_sub, n_ctas):
+    """The refresh at ragged region sizes and several CTA counts, where the
+    correction's work (the upper triangle of W row by row, two rows per warp;
+    the active rows above each block of 32 columns) is dealt over the grid in
+    snake order and the own rows gather the sums after a grid barrier: after
+    16 kept flips, the 16th followed by a fold and a refresh, e and T are at
+    FP64-level error against direct solves of the current design."""
+    case = fdfd256 if n_sub == fdfd256.n_d else fdfd256.sub_case(np.arange(n_sub))
+    b0 = W.random_design(case.n_d, 11)
+    ctx = _ctx(P, case, mode=P.PNGF_BEST_IMPROVEMENT, tau=1e-9, delay_r=16, refresh_k=16, n_ctas=n_ctas)
+    ctx.factor(b0)
+    cnt = ctx.dbs_sweep(16)["counters"]
+    assert int(cnt[0]) == 16 and int(cnt[4]) == 1
+    b = ctx.design()
+    v = case.dv * b
+    st = ctx.state()
+    err = max(rel(st["e"], O.solve_field(case.G_dd, case.c_d, v)),
+              rel(st["T"], O.port_projection(case.G_dd, case.G_od, v)))
+    print(f"n_d {case.n_d}, {n_ctas} CTAs: refreshed state error {err:.3e}")
+    assert err < 1e-11
+    ctx.close()
+
+
 @pytest.mark.parametrize("n_accepts", [3, 8, 13])
 def test_mixed_accepts_follow_resolves(P, fdfd64, n_accepts):
     """Standalone accepts across a flush (delay_r = 4)."""
