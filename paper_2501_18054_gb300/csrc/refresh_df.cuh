@@ -170,6 +170,25 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
   const int nst = (m + S - 1) / S;
   const unsigned s0 = (unsigned)__cvta_generic_to_shared(area);
   const bool live = grp < ng;
+  // this lane's x copies: the same slots and source offsets every stage, the list position
+  // moving by S (x_t: position within a stage, -1 = none)
+  constexpr int XMAX = (2 * 9 * RD_RMAX + 31) / 32;
+  int x_t[XMAX];
+  unsigned x_dst[XMAX];
+  size_t x_src[XMAX];
+#pragma unroll
+  for (int u = 0; u < XMAX; ++u) {
+    const int e = lane + 32 * u;
+    x_t[u] = -1;
+    x_dst[u] = 0;
+    x_src[u] = 0;
+    if (e < 2 * NV * R) {
+      const int h = e & 1, qr = e >> 1, q = qr / R, r = qr - q * R;
+      x_t[u] = grp + ng * r;
+      x_dst[u] = oX + (unsigned)(((warp * NV + q) * R + r) * 2 + h) * 16u;
+      x_src[u] = 2 * (size_t)q * a.n + h;
+    }
+  }
   // this thread's copies of stage k into slot k % RD_D (always one cp.async group)
   auto issue = [&](int k) {
     if (live && k < nst) {
@@ -182,12 +201,11 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
                      "l"(src)
                      : "memory");
       }
-      for (int e = lane; e < 2 * NV * R; e += 32) {
-        const int h = e & 1, qr = e >> 1, q = qr / R, r = qr - q * R, t = k * S + grp + ng * r;
-        if (t < m)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                           dst + oX + (unsigned)(((warp * NV + q) * R + r) * 2 + h) * 16u),
-                       "l"(a.xs + 2 * ((size_t)q * a.n + t) + h)
+#pragma unroll
+      for (int u = 0; u < XMAX; ++u) {
+        const int t = k * S + x_t[u];
+        if (x_t[u] >= 0 && t < m)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + x_dst[u]), "l"(a.xs + x_src[u] + 2 * t)
                        : "memory");
       }
     }
@@ -208,8 +226,8 @@ __device__ __noinline__ void refresh_residual_df_t(const SweepArgs& a, int pb, i
     const unsigned char* st = area + (size_t)(k % RD_D) * stage;
     const ulonglong2* gst = reinterpret_cast<const ulonglong2*>(st) + grp * R * gs + jl;
     const ulonglong2* xst = reinterpret_cast<const ulonglong2*>(st + oX) + warp * NV * R * 2;
-    for (int r = 0; r < R; ++r) {
-      if (k * S + grp + ng * r >= m) break;
+    const int tk = k * S + grp, rc = tk < m ? min(R, (m - tk + ng - 1) / ng) : 0;
+    for (int r = 0; r < rc; ++r) {
       const ulonglong2 g = gst[r * gs];  // (Re hi, Im hi), (Re lo, Im lo) of G
       float gr1, gi1, gr2, gi2;
       upk2(g.x, gr1, gi1);
