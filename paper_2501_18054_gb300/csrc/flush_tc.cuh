@@ -10,18 +10,19 @@
 // memory, which keeps the fold at FP32 accuracy (the rounding of W_lo itself).
 //
 // Data flow per tile (128 rows x 64 NB columns, both planes; NB = 2 for the
-// persistent search, whose A chunk then serves twice as many outputs):
+// persistent search, 1 for the batch kernel):
 //   1. a prepare pass writes the split operands once per fold into global
 //      images laid out exactly as the shared-memory tiles (K-major, no
-//      swizzle: 8-row x 16-byte core matrices, 128 B apart along K, 1024 B
-//      apart along the rows);
+//      swizzle: 8-row x 16-byte core matrices, 128 B apart along K, 512 B
+//      apart along the rows), in blocks of 128 rows for both operands;
 //   2. per K-chunk of 16, one bulk asynchronous copy (cp.async.bulk, the TMA
 //      engine) per operand brings the images into one of two shared-memory
 //      buffers, completing that buffer's mbarrier transaction count; the copy
 //      of chunk c + 1 runs while the tensor cores work on chunk c;
-//   3. one thread issues tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8)
-//      into two 64-column accumulators in tensor memory and commits to the
-//      buffer's MMA mbarrier;
+//   3. one thread issues tcgen05.mma (kind::tf32, M = 128, N = 64 NB, K = 8:
+//      twelve per K-step, the 3xTF32 terms of the four real products) into
+//      the tile's accumulator in tensor memory (Dr and Di, 64 NB columns
+//      each) and commits to the buffer's MMA mbarrier;
 //   4. the tile of W_lo is read into registers when the tile starts; four
 //      warps read the accumulators back with tcgen05.ld and stage them in
 //      shared memory, and every thread adds them into its part of the tile.
@@ -35,24 +36,27 @@ namespace pngf {
 namespace {
 
 constexpr int TC_M = 128;            // rows of an output tile (MMA M)
-constexpr int TC_N = 64;             // columns of an output tile (MMA N)
+constexpr int TC_N = 128;            // rows of a B image block (a tile covers 64 NB of them)
 constexpr int TC_KC = 16;            // delayed columns per K-chunk
-constexpr int TC_ASUB = TC_M * TC_KC * 4;  // one A sub-image (hi or lo, re or im): 16 KB
-constexpr int TC_BSUB = TC_N * TC_KC * 4;  // one B sub-image: 8 KB
+constexpr int TC_ASUB = TC_M * TC_KC * 4;  // one A sub-image (hi or lo, re or im): 8 KB
+constexpr int TC_BSUB = TC_N * TC_KC * 4;  // one B sub-image of a global block: 8 KB
 constexpr int TC_ACHUNK = 4 * TC_ASUB;     // Yr_hi, Yr_lo, Yi_hi, Yi_lo
 constexpr int TC_BCHUNK = 4 * TC_BSUB;     // Xr_hi, Xr_lo, Xi_hi, Xi_lo
 constexpr int TC_NBUF = 2;                      // operand buffers
 constexpr int TC_PREF = 1;                      // chunks copied ahead of the one multiplied
 constexpr int TC_PC = 16;                       // tile columns per epilogue part
 constexpr int TC_STAGE = 2 * TC_M * TC_PC * 4;  // one part of both planes: 16 KB
-// A tile of the fold is 128 rows x 64 NB columns: NB 64-row blocks of X
-// (B operand) share one 128-row block of Y (A operand), NB = 1 or 2.
-__host__ __device__ constexpr int tc_buf_bytes(int nb) { return TC_ACHUNK + nb * TC_BCHUNK; }  // 48 / 64 KB
+// A tile of the fold is 128 rows x 64 NB columns: one 128-row block of Y (A
+// operand) against 64 NB rows of X (B operand, the whole of a 128-row image
+// block for NB = 2, one half of it for NB = 1), NB = 1 or 2.
+__host__ __device__ constexpr int tc_tile_cols(int nb) { return 64 * nb; }
+__host__ __device__ constexpr int tc_bsub_smem(int nb) { return tc_tile_cols(nb) * TC_KC * 4; }  // 4 / 8 KB
+__host__ __device__ constexpr int tc_buf_bytes(int nb) { return TC_ACHUNK + 4 * tc_bsub_smem(nb); }  // 48 / 64 KB
 // float4 slot of stage row `row`, column group q4 (4 columns): the XOR spreads
 // both the row-per-lane writes and the row-contiguous reads over all banks
 __device__ __forceinline__ int tc_stage_slot(int row, int q4) { return row * 4 + (q4 ^ ((row >> 1) & 3)); }
 __host__ __device__ constexpr int tc_fold_smem(int nb) { return TC_NBUF * tc_buf_bytes(nb) + TC_STAGE; }
-// tensor memory: two accumulators of NB x (Dr: 64 columns, Di: 64 columns)
+// tensor memory: two accumulators of (Dr: 64 NB columns, Di: 64 NB columns)
 __host__ __device__ constexpr int tc_tmem_cols(int nb) { return 2 * 128 * nb; }
 constexpr unsigned long long kTcSpin = 1ull << 22;
 
@@ -81,9 +85,9 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned smem_addr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A = B = TF32, K-major, N = 64, M = 128
-__device__ __forceinline__ unsigned tc_idesc(bool negate_a) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_a ? 1u : 0u) << 13) | ((unsigned)(TC_N >> 3) << 17) |
+// instruction descriptor: D = F32, A = B = TF32, K-major, N = n_cols, M = 128
+__device__ __forceinline__ unsigned tc_idesc(bool negate_a, int n_cols) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_a ? 1u : 0u) << 13) | ((unsigned)(n_cols >> 3) << 17) |
          ((unsigned)(TC_M >> 4) << 24);
 }
 
@@ -109,20 +113,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned phase) {
   return false;
 }
 
-// 64-row blocks of the B image, padded to an even count (the pad holds zeros)
-__host__ __device__ __forceinline__ int tc_nj64(int n) { return ((n + TC_N - 1) / TC_N + 1) & ~1; }
+// 128-row blocks of the B image
+__host__ __device__ __forceinline__ int tc_njb(int n) { return (n + TC_N - 1) / TC_N; }
 
-// number of tiles (128-row block ti, 64 NB-column block tj >= 2 ti / NB) and the tile of index t
+// number of tiles of the upper triangle (128-row block ti, 64 NB-column block
+// tj >= 2 ti / NB) and the tile of index t
 template <int NB>
 __device__ __forceinline__ long long tc_tiles(int n) {
-  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N * NB - 1) / (TC_N * NB);
+  static_assert(NB == 1 || NB == 2, "tiles of 128 x 64 or 128 x 128");
+  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + tc_tile_cols(NB) - 1) / tc_tile_cols(NB);
   long long T = 0;
   for (int ti = 0; ti < nI; ++ti) T += max(0, nJ - 2 * ti / NB);
   return T;
 }
 template <int NB>
 __device__ __forceinline__ void tc_tile(long long t, int n, int& ti, int& tj) {
-  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + TC_N * NB - 1) / (TC_N * NB);
+  const int nI = (n + TC_M - 1) / TC_M, nJ = (n + tc_tile_cols(NB) - 1) / tc_tile_cols(NB);
   for (ti = 0; ti < nI; ++ti) {
     long long cnt = max(0, nJ - 2 * ti / NB);
     if (t < cnt) {
@@ -149,8 +155,8 @@ __device__ __forceinline__ void tc_store_split(unsigned char* base, int sub, con
 }
 
 // Prepare pass (all threads of the calling grid, items split round-robin):
-// split images of Y = X diag(alpha) (A side, 128-row blocks) and X (B side,
-// 64-row blocks), for nk = ceil(r / TC_KC) chunks, zero-padded past n and r.
+// split images of Y = X diag(alpha) (A side) and X (B side), both in 128-row
+// blocks, for nk = ceil(r / TC_KC) chunks, zero-padded past n and r.
 // An item is four consecutive delayed columns of one row: one 32-byte read of
 // X and one 16-byte write per sub-image (four k of a core-matrix row).
 __device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char* imgA, unsigned char* imgB,
@@ -162,7 +168,7 @@ __device__ __noinline__ void tc_prepare(const SweepArgs& a, int r, unsigned char
   }
   __syncthreads();
   const int n = a.n, nk = (r + TC_KC - 1) / TC_KC;
-  const unsigned nI = (unsigned)(n + TC_M - 1) / TC_M, nJ = (unsigned)tc_nj64(n);
+  const unsigned nI = (unsigned)(n + TC_M - 1) / TC_M, nJ = (unsigned)tc_njb(n);
   constexpr unsigned KQ = TC_KC / 4;  // items per chunk row
   // A side: item = ((I * nk + c) * TC_M + row) * KQ + kq
   const unsigned totA = nI * (unsigned)nk * TC_M * KQ;
@@ -283,7 +289,9 @@ __device__ __forceinline__ void tc_teardown(TcState& st, bool failed) {
 }
 
 // producer: bulk copies of K-chunk c of tile (ti, tj) into buffer bf: the A
-// chunk of row block ti, then the B chunks of the NB column blocks NB tj + s
+// chunk of row block ti, then the B chunk of the tile's 64 NB columns (NB = 2:
+// image block tj in one copy; NB = 1: half tj & 1 of image block tj / 2, one
+// copy per sub-image)
 template <int NB>
 __device__ __forceinline__ void tc_issue_copy(TcState& st, int bf, unsigned sbuf, const unsigned char* imgA,
                                               const unsigned char* imgB, int ti, int tj, int c, int nk) {
@@ -293,53 +301,58 @@ __device__ __forceinline__ void tc_issue_copy(TcState& st, int bf, unsigned sbuf
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbuf),
                "l"(ga), "r"(TC_ACHUNK), "r"(mb)
                : "memory");
-#pragma unroll
-  for (int sb = 0; sb < NB; ++sb) {
-    const unsigned char* gb = imgB + ((size_t)(NB * tj + sb) * nk + c) * TC_BCHUNK;
+  if (NB == 2) {
+    const unsigned char* gb = imgB + ((size_t)tj * nk + c) * TC_BCHUNK;
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     sbuf + TC_ACHUNK + sb * TC_BCHUNK),
+                     sbuf + TC_ACHUNK),
                  "l"(gb), "r"(TC_BCHUNK), "r"(mb)
                  : "memory");
+  } else {
+    const unsigned char* gb = imgB + ((size_t)(tj >> 1) * nk + c) * TC_BCHUNK + (size_t)(tj & 1) * tc_bsub_smem(1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       sbuf + TC_ACHUNK + q * tc_bsub_smem(1)),
+                   "l"(gb + (size_t)q * TC_BSUB), "r"(tc_bsub_smem(1)), "r"(mb)
+                   : "memory");
   }
   st.pend[TC_B_LOAD + bf] = 1;
 }
 
 // producer: the 3xTF32 products of one K-chunk (buffer sbuf) into accumulator
-// dacc (B block s: Dr at dacc + 128 s, Di at dacc + 128 s + 64); commits to
-// TC_B_FREE + bf, and to TC_B_FULL + acc after the tile's last chunk
+// dacc (Dr at dacc, Di at dacc + 64 NB); commits to TC_B_FREE + bf, and to
+// TC_B_FULL + acc after the tile's last chunk.  The descriptors of the eight
+// sub-images differ from the buffer's by constant start offsets.
 template <int NB>
 __device__ __forceinline__ void tc_issue_mma(TcState& st, int bf, unsigned sbuf, unsigned dacc, bool first_chunk,
                                              bool last_chunk, int acc) {
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const unsigned sA = sbuf;
-  const unsigned id_pos = tc_idesc(false), id_neg = tc_idesc(true);
+  constexpr int TN = tc_tile_cols(NB), BS = tc_bsub_smem(NB);
+  const unsigned id_pos = tc_idesc(false, TN), id_neg = tc_idesc(true, TN);
+  const unsigned long long d0 = tc_desc(sbuf);  // start field: address >> 4 (buffers end below 256 KB)
+  const unsigned dR = dacc, dI = dacc + TN;
 #pragma unroll
   for (int ks = 0; ks < TC_KC / 8; ++ks) {
-    const unsigned ko = 256u * ks;
-    const unsigned long long yr_hi = tc_desc(sA + 0 * TC_ASUB + ko), yr_lo = tc_desc(sA + 1 * TC_ASUB + ko);
-    const unsigned long long yi_hi = tc_desc(sA + 2 * TC_ASUB + ko), yi_lo = tc_desc(sA + 3 * TC_ASUB + ko);
+    const unsigned long long dk = d0 + (unsigned long long)((256u * ks) >> 4);
+    const unsigned long long yr_hi = dk + (0 * TC_ASUB >> 4), yr_lo = dk + (1 * TC_ASUB >> 4);
+    const unsigned long long yi_hi = dk + (2 * TC_ASUB >> 4), yi_lo = dk + (3 * TC_ASUB >> 4);
+    const unsigned long long xr_hi = dk + ((TC_ACHUNK + 0 * BS) >> 4), xr_lo = dk + ((TC_ACHUNK + 1 * BS) >> 4);
+    const unsigned long long xi_hi = dk + ((TC_ACHUNK + 2 * BS) >> 4), xi_lo = dk + ((TC_ACHUNK + 3 * BS) >> 4);
     const unsigned first = (first_chunk && ks == 0) ? 0u : 1u;
-#pragma unroll
-    for (int sb = 0; sb < NB; ++sb) {
-      const unsigned sB = sbuf + TC_ACHUNK + sb * TC_BCHUNK;
-      const unsigned long long xr_hi = tc_desc(sB + 0 * TC_BSUB + ko), xr_lo = tc_desc(sB + 1 * TC_BSUB + ko);
-      const unsigned long long xi_hi = tc_desc(sB + 2 * TC_BSUB + ko), xi_lo = tc_desc(sB + 3 * TC_BSUB + ko);
-      const unsigned dR = dacc + 128u * sb, dI = dR + TC_N;
-      // Wr += Yr Xr^T - Yi Xi^T
-      tc_mma(dR, yr_hi, xr_hi, id_pos, first);
-      tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
-      tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
-      tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
-      tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
-      tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
-      // Wi += Yr Xi^T + Yi Xr^T
-      tc_mma(dI, yr_hi, xi_hi, id_pos, first);
-      tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
-      tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
-      tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
-      tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
-      tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
-    }
+    // Wr += Yr Xr^T - Yi Xi^T
+    tc_mma(dR, yr_hi, xr_hi, id_pos, first);
+    tc_mma(dR, yr_hi, xr_lo, id_pos, 1);
+    tc_mma(dR, yr_lo, xr_hi, id_pos, 1);
+    tc_mma(dR, yi_hi, xi_hi, id_neg, 1);
+    tc_mma(dR, yi_hi, xi_lo, id_neg, 1);
+    tc_mma(dR, yi_lo, xi_hi, id_neg, 1);
+    // Wi += Yr Xi^T + Yi Xr^T
+    tc_mma(dI, yr_hi, xi_hi, id_pos, first);
+    tc_mma(dI, yr_hi, xi_lo, id_pos, 1);
+    tc_mma(dI, yr_lo, xi_hi, id_pos, 1);
+    tc_mma(dI, yi_hi, xr_hi, id_pos, 1);
+    tc_mma(dI, yi_hi, xr_lo, id_pos, 1);
+    tc_mma(dI, yi_lo, xr_hi, id_pos, 1);
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    st.mb[TC_B_FREE + bf])
@@ -455,7 +468,7 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
     for (long long k = 0; k < my_tiles && ok; ++k) {
       int ti, tj;
       tc_tile<NB>(t_begin + k * t_step, n, ti, tj);
-      const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * TC_N * NB;
+      const int acc = (int)(k & 1), i0 = ti * TC_M, j0 = tj * tc_tile_cols(NB);
       for (int h = 0; h < 4 * NB && ok; ++h) {  // 16-column parts of the tile
         // which of this thread's four-column items of the part lie inside W (2: all four, 1: some)
         int okv[4];
@@ -477,13 +490,12 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
             break;
           }
         }
-        // accumulator rows of this warp's quadrant -> stage (Dr at column 0 of the
-        // 64-row block h / 4, Di 64 further)
+        // accumulator rows of this warp's quadrant -> stage (Dr at column 16 h, Di 64 NB further)
         const int row = 32 * quad + lane;
-        const unsigned addr = st.tmem + lane_base + ACC * acc + 128u * (h >> 2) + (unsigned)(TC_PC * (h & 3));
+        const unsigned addr = st.tmem + lane_base + ACC * acc + (unsigned)(TC_PC * h);
         for (int pl = pl0; pl < 2; pl += wpq) {
           float v[16];
-          tc_ld16(addr + TC_N * pl, v);
+          tc_ld16(addr + tc_tile_cols(NB) * pl, v);
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4)
             stage[pl * TC_M * 4 + tc_stage_slot(row, q4)] =
@@ -529,7 +541,7 @@ __device__ __noinline__ bool tc_fold_tiles(const SweepArgs& a, int r, const unsi
 // bytes of the global operand images for a region of n pixels and r <= R delayed columns
 __host__ __device__ __forceinline__ size_t tc_image_bytes(int n, int R) {
   const size_t nk = (size_t)(R + TC_KC - 1) / TC_KC;
-  const size_t nI = (size_t)(n + TC_M - 1) / TC_M, nJ = (size_t)tc_nj64(n);
+  const size_t nI = (size_t)(n + TC_M - 1) / TC_M, nJ = (size_t)tc_njb(n);
   return nI * nk * TC_ACHUNK + nJ * nk * TC_BCHUNK;
 }
 
