@@ -7,8 +7,11 @@
 // design region, possibly of a different size, its own W, state and trace),
 // and one CTA advances one run at a time through the whole search: scoring,
 // selection, the kept-flip update, the FP64 refresh and, on the mixed path,
-// the flush of the delayed set, with only CTA-wide barriers.  Runs are dealt
-// to CTAs round-robin; all runs of a batch share one stream.
+// the flush of the delayed set, with only CTA-wide barriers.  All runs of a
+// batch share one stream.  The runs wait in a queue, largest region first, and
+// one CTA per SM takes the next run whenever it finishes one (an atomic
+// counter): a large run then has its SM's FP64 pipe to itself, and the small
+// runs fill the other SMs (longest-processing-time-first list scheduling).
 //
 // FIRST mode scores the visiting positions in chunks of blockDim starting at
 // the current position and keeps the earliest improving one (the same
@@ -17,6 +20,8 @@
 #include <cstdio>
 #include <memory>
 #include <new>
+#include <algorithm>
+#include <vector>
 
 #include "flush_tc.cuh"
 
@@ -62,7 +67,8 @@ __device__ void cta_refresh(const SweepArgs& a, const ObjParams& op, c128* s_o, 
   cta_ports(a, op, s_o, s_f);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const SweepArgs* __restrict__ runs, int n_runs) {
+__global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const SweepArgs* __restrict__ runs, int n_runs,
+                                                                      int* __restrict__ queue) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ c128 s_o[kMaxPorts];
   __shared__ double s_f;
@@ -78,7 +84,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
   TcState tcs{};
   if (use_tc) tc_setup(tcs, s_tc_bars, &s_tmem, tc_tmem_cols(1));
   bool tc_failed = false;
-  for (int run = blockIdx.x; run < n_runs && !tc_failed; run += gridDim.x) {
+  __shared__ int s_run;
+  while (!tc_failed) {
+    __syncthreads();  // every thread has read the previous s_run
+    if (threadIdx.x == 0) s_run = atomicAdd(queue, 1);
+    __syncthreads();
+    const int run = s_run;
+    if (run >= n_runs) break;
     const SweepArgs& a = runs[run];
     const int n = a.n;
     Control* ctl = a.ctl;
@@ -305,20 +317,27 @@ __global__ void write_args_kernel(const ArgChunk ch, SweepArgs* __restrict__ dst
 
 }  // namespace
 
-size_t batch_workspace_bytes(int n_runs) { return ((size_t)n_runs * sizeof(SweepArgs) + 255) / 256 * 256; }
+// the argument table, then the run queue's counter
+static size_t batch_table_bytes(int n_runs) { return ((size_t)n_runs * sizeof(SweepArgs) + 255) / 256 * 256; }
+size_t batch_workspace_bytes(int n_runs) { return batch_table_bytes(n_runs) + 256; }
 
 pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, const int32_t* const* orders,
                             int32_t* const* traces, double* const* trace_f, int32_t trace_cap, int64_t* counters,
                             void* ws, size_t ws_bytes) {
   pngf_ctx* c0 = ctxs[0];
   SweepArgs* table = static_cast<SweepArgs*>(ws);
+  int* queue = reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + batch_table_bytes(n_runs));
   std::unique_ptr<ArgChunk> ch(new (std::nothrow) ArgChunk());
   if (!ch) return PNGF_ENOMEM;
+  // queue order: largest region first (ties: the caller's order)
+  std::vector<int> rank(n_runs);
+  for (int r = 0; r < n_runs; ++r) rank[r] = r;
+  std::stable_sort(rank.begin(), rank.end(), [&](int x, int y) { return ctxs[x]->cfg.n_d > ctxs[y]->cfg.n_d; });
   int max_n = 0;
   for (int r0 = 0; r0 < n_runs; r0 += kArgChunk) {
     ch->count = n_runs - r0 < kArgChunk ? n_runs - r0 : kArgChunk;
     for (int i = 0; i < ch->count; ++i) {
-      const int r = r0 + i;
+      const int r = rank[r0 + i];
       SweepArgs a = make_args(ctxs[r]);
       a.n_sweeps = n_sweeps;
       a.order = orders ? orders[r] : nullptr;
@@ -336,12 +355,10 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
   size_t smem = mixed ? (kFlushSmem > (size_t)tc_fold_smem(1) ? kFlushSmem : (size_t)tc_fold_smem(1)) : (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PNGF_ECUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbs_batch_kernel, kBatchThreads, smem);
-  if (per_sm < 1) per_sm = 1;
-  int grid = c0->n_sm * per_sm;
+  if (cudaMemsetAsync(queue, 0, sizeof(int), c0->stream) != cudaSuccess) return PNGF_ECUDA;
+  int grid = c0->n_sm;  // one CTA per SM
   if (grid > n_runs) grid = n_runs;
-  dbs_batch_kernel<<<grid, kBatchThreads, smem, c0->stream>>>(static_cast<const SweepArgs*>(ws), n_runs);
+  dbs_batch_kernel<<<grid, kBatchThreads, smem, c0->stream>>>(static_cast<const SweepArgs*>(ws), n_runs, queue);
   return cuda_status(cudaGetLastError());
 }
 
