@@ -234,6 +234,9 @@ pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order
  *   counters  int64 n_ctx x 8 (device, out), per run as in pngf_dbs_sweep
  *   batch_ws  device scratch of pngf_batch_workspace_size(n_ctx) bytes, 256-byte aligned
  * Each run follows the same semantics as pngf_dbs_sweep on its own context.
+ * Scheduling (no effect on the results): one CTA per SM takes the runs from a
+ * queue in descending n_d (ties in the given order), so that the largest runs
+ * start first, each on an SM of its own.
  */
 /* n_d <= PNGF_BATCH_MAX_ND for every run: the FP64 batch kernel stages one
  * run's gathered column in 16 x n_d bytes of shared memory (64 KiB at the
