@@ -135,3 +135,39 @@ def test_batch_rejects_mixed_contexts(P):
     with pytest.raises(P.PngfError) as ei:
         P.DbsBatch([a, b]).dbs_sweep(1)
     assert ei.value.status == P.PNGF_EINVAL
+
+
+def test_batch_queue_many_ragged_runs(P):
+    """More runs than SMs, of four region sizes in mixed order: the runs go
+    through the batch call's queue (largest region first, one CTA per SM taking
+    the next run), and every run still ends bit for bit as the same run done
+    alone, whatever the order in which the caller lists them."""
+    fdfd64 = W.get_case("fdfd64")
+    rng = np.random.default_rng(11)
+    sizes = [100, 64, 37, 16]
+    subs = {n: (fdfd64 if n == 100 else fdfd64.sub_case(np.sort(rng.choice(100, n, False)))) for n in sizes}
+    n_runs = 176  # above the 152 SMs of the part
+    spec = [(sizes[(7 * i) % 4], i) for i in range(n_runs)]
+    kw = dict(precision=P.PNGF_FP64, tau=1e-9, refresh_k=0)
+    solo = []
+    for n, seed in spec:
+        c = P.DbsContext(subs[n], **kw)
+        c.factor(W.random_design(n, seed))
+        r = c.dbs_sweep(3)
+        solo.append(([int(x[2]) for x in r["trace"]], c.eval_ports()[0], c.design()))
+        c.close()
+    for perm in (np.arange(n_runs), rng.permutation(n_runs)):
+        ctxs = [None] * n_runs
+        for i in perm:
+            n, seed = spec[i]
+            c = P.DbsContext(subs[n], **kw)
+            c.factor(W.random_design(n, seed))
+            ctxs[i] = c
+        res = P.DbsBatch([ctxs[i] for i in perm]).dbs_sweep(3)
+        for pos, i in enumerate(perm):
+            k_s, o_s, b_s = solo[i]
+            assert [int(x[2]) for x in res[pos]["trace"]] == k_s, i
+            o, _ = ctxs[i].eval_ports()
+            assert np.array_equal(o, o_s) and np.array_equal(ctxs[i].design(), b_s), i
+        for c in ctxs:
+            c.close()
