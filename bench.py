@@ -120,6 +120,8 @@ def parse():
     ap.add_argument("--hankel-sweeps", type=int, default=2,
                     help="hankel128_nd16384: sweeps per run (the third drives the lossless design into a "
                          "high-Q resonance where the FP32 inverse of the mixed path stops with PNGF_EACCURACY)")
+    ap.add_argument("--side-runs", type=int, default=8,
+                    help="pec/tiles/multifreq workloads: independent searches side by side (nsm / runs CTAs each)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="mixed path: choose runs per GPU, delay R and fold engine from timed trials first")
     return ap.parse_args()
@@ -635,31 +637,53 @@ def bench_side(args, torch, dist, dev, P, Wl):
             else:
                 cases = [Wl.get_case(base)]
             prec = P.PNGF_PEC if name.startswith("pec") else P.PNGF_FP64
-            b0 = Wl.random_design(cases[0].n_d, 0)
-            for c in cases:
-                cx = P.DbsContext(c, precision=prec, tau=tau, refresh_k=args.refresh_k, device=str(dev), stream=stream)
-                cx.factor(b0)
-                cx.snapshot()
-                ctxs.append(cx)
             n = cases[0].n_d
-            cnt = torch.zeros(8, dtype=torch.int64, device=dev)
-            if name.startswith("pec"):
-                def step():
-                    P.pngf_restore(ctxs[0].ctx)
-                    P.pngf_dbs_sweep(ctxs[0].ctx, sweeps, None, None, None, 0, cnt.data_ptr())
-            else:
+            # independent searches (seeds 0 .. runs - 1) side by side, each a cooperative
+            # launch of nsm / runs CTAs on its own stream
+            n_side = max(1, args.side_runs)
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            ctas = nsm // n_side if n_side > 1 else 0
+            tiles = None
+            if not name.startswith("pec"):
                 tiles = (Wl.square_tiles(32, 32, 2) if name.startswith("tiles")
                          else np.arange(n, dtype=np.int32)[:, None])
-                ts = P.TileSearch(ctxs, tiles, combine=P.PNGF_COMBINE_MEAN)
-                extra["tile_m"], extra["n_tiles"], extra["systems"] = int(ts.tile_m), int(ts.n_tiles), len(ctxs)
+            sets = []
+            for i in range(n_side):
+                s_i = torch.cuda.Stream(dev)
+                b0 = Wl.random_design(n, i)
+                cx_i = []
+                for c in cases:
+                    cx = P.DbsContext(c, precision=prec, tau=tau, refresh_k=args.refresh_k, device=str(dev),
+                                      stream=s_i, n_ctas=ctas)
+                    cx.factor(b0)
+                    cx.snapshot()
+                    cx_i.append(cx)
+                    ctxs.append(cx)
+                ts = P.TileSearch(cx_i, tiles, combine=P.PNGF_COMBINE_MEAN) if tiles is not None else None
+                sets.append((s_i, cx_i, ts, torch.zeros(8, dtype=torch.int64, device=dev)))
+            torch.cuda.synchronize(dev)
+            if tiles is not None:
+                ts0 = sets[0][2]
+                extra["tile_m"], extra["n_tiles"], extra["systems"] = int(ts0.tile_m), int(ts0.n_tiles), len(cases)
+            extra["runs"], extra["ctas_per_run"] = n_side, ctas if ctas else nsm
 
-                def step():
-                    for cx in ctxs:
+            def step():
+                fork = torch.cuda.Event()
+                fork.record(stream)
+                for s_i, cx_i, ts, cnt_i in sets:
+                    s_i.wait_event(fork)
+                    for cx in cx_i:
                         P.pngf_restore(cx.ctx)
-                    P.pngf_dbs_sweep_tiles([cx.ctx for cx in ctxs], ts.combine, ts.tiles.data_ptr(), ts.n_tiles,
-                                           ts.tile_m, sweeps, None, None, None, 0, cnt.data_ptr(), ts.ws.data_ptr(),
-                                           ts.ws_bytes)
-            unit, per = UNIT, 1
+                    if ts is None:
+                        P.pngf_dbs_sweep(cx_i[0].ctx, sweeps, None, None, None, 0, cnt_i.data_ptr())
+                    else:
+                        P.pngf_dbs_sweep_tiles([cx.ctx for cx in cx_i], ts.combine, ts.tiles.data_ptr(), ts.n_tiles,
+                                               ts.tile_m, sweeps, None, None, None, 0, cnt_i.data_ptr(),
+                                               ts.ws.data_ptr(), ts.ws_bytes)
+                    j = torch.cuda.Event()
+                    j.record(s_i)
+                    stream.wait_event(j)
+            unit, per = UNIT, n_side
         for _ in range(max(args.warmup, 1)):
             step()
         stream.synchronize()
@@ -667,7 +691,7 @@ def bench_side(args, torch, dist, dev, P, Wl):
             if cx.sync() != 0:
                 raise RuntimeError(f"{name}: warm-up failed")
         if name != "gradient_fdfd256_nd4096":
-            c0 = cnt.cpu().numpy().copy()
+            c0 = sum(st[3].cpu().numpy() for st in sets)
             units = float(c0[1])
         torch.cuda.synchronize(dev)
         clocks = Clocks(dist.local)
@@ -696,7 +720,8 @@ def bench_side(args, torch, dist, dev, P, Wl):
         accepts = None
         extra["us_per_gradient"] = ms * 1e3 / reps
     else:
-        c1 = cnt.cpu().numpy()
+        c1 = sum(st[3].cpu().numpy() for st in sets)
+        assert int(c1[1]) == int(c0[1]), "steps are not identical searches"
         accepts = int(c1[0])
         tri = n * (n + 1) / 2
         if name.startswith("pec"):
@@ -704,7 +729,7 @@ def bench_side(args, torch, dist, dev, P, Wl):
             kern = "dbs_pec_kernel"
         else:
             m = extra["tile_m"]
-            flops = accepts * len(ctxs) * 8.0 * m * tri  # rank-m update of every system's triangle
+            flops = accepts * len(cases) * 8.0 * m * tri  # rank-m update of every system's triangle
             kern = "dbs_tiles_kernel"
         gf = flops / (ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": gf / 1e3, "peak": peak_fp64 / 1e3, "unit": "TFLOP/s",
@@ -715,7 +740,8 @@ def bench_side(args, torch, dist, dev, P, Wl):
                 n_gpus=dist.world, steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config={"workload": name, "what": SIDE_WORKLOADS[name], "max_sweeps": sweeps,
-                        "step": "restore the factored start + one search (or %d gradients)" % per, **extra},
+                        "step": ("restore the factored start + one search on each of %d concurrent runs" % per
+                                 if unit == UNIT else "%d gradients" % per), **extra},
                 roofline=roof, accepts_per_step=accepts, clocks=clk, gpu_launches=args.steps * per,
                 cpu_baseline=None, e2e=None)
     if dist.rank == 0:
