@@ -239,8 +239,9 @@ pngf_status pngf_dbs_sweep(pngf_ctx* ctx, int32_t n_sweeps, const int32_t* order
  * start first, each on an SM of its own.
  */
 /* n_d <= PNGF_BATCH_MAX_ND for every run: the FP64 batch kernel stages one
- * run's gathered column in 16 x n_d bytes of shared memory (64 KiB at the
- * bound), so a larger region returns PNGF_EINVAL before any launch. */
+ * run's gathered column and the column times alpha in 32 x n_d bytes of shared
+ * memory (128 KiB at the bound), so a larger region returns PNGF_EINVAL before
+ * any launch. */
 #define PNGF_BATCH_MAX_RUNS 65536
 #define PNGF_BATCH_MAX_ND 4096
 pngf_status pngf_batch_workspace_size(int32_t n_ctx, size_t* bytes);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "flush_tc.cuh"
+#include "rank1.cuh"
 
 namespace pngf {
 namespace {
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
     int r = ctl->r_delay;
     int s = 0, t = 0, acc_in_sweep = 0;
     const long long E = (long long)n * (n + 1) / 2;
-    c128* cs = reinterpret_cast<c128*>(dyn);  // FP64 path: the gathered column
+    c128* cs = reinterpret_cast<c128*>(dyn);  // FP64 path: the gathered column c, then alpha c
+    c128* acs = cs + n;
     while (true) {
       const double f = s_f;
       const double thr = accept_threshold(s_op, f);
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
           c128 cj = cs[j];
           c128 aj = cmul(s_pv.alpha, cj);
+          acs[j] = aj;
           a.diag[j] = cfma(aj, cj, a.diag[j]);
           a.e[j] = cfma(s_pv.coef, cj, a.e[j]);
           for (int p = 0; p < a.n_o; ++p) {
@@ -227,7 +230,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) dbs_batch_kernel(const Sweep
             a.v[j] = nb ? a.dv[j] : mk(0.0, 0.0);
           }
         }
-        rank1_upper(a.W, n, a.ldw, cs, s_pv.alpha, 0, E);
+        __syncthreads();  // every alpha c_j formed
+        rank1_upper_ac(a.W, n, a.ldw, acs, cs, 0, E);
         __syncthreads();
         ++since_refresh;
         if (a.refresh_k > 0 && since_refresh >= a.refresh_k) {
@@ -352,7 +356,8 @@ pngf_status run_sweep_batch(pngf_ctx* const* ctxs, int n_runs, int n_sweeps, con
     if (cudaGetLastError() != cudaSuccess) return PNGF_ECUDA;
   }
   const bool mixed = c0->cfg.precision == PNGF_MIXED;
-  size_t smem = mixed ? (kFlushSmem > (size_t)tc_fold_smem(1) ? kFlushSmem : (size_t)tc_fold_smem(1)) : (size_t)max_n * sizeof(c128);
+  size_t smem = mixed ? (kFlushSmem > (size_t)tc_fold_smem(1) ? kFlushSmem : (size_t)tc_fold_smem(1))
+                      : 2 * (size_t)max_n * sizeof(c128);
   if (cudaFuncSetAttribute(dbs_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PNGF_ECUDA;
   if (cudaMemsetAsync(queue, 0, sizeof(int), c0->stream) != cudaSuccess) return PNGF_ECUDA;

@@ -22,7 +22,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "sweep_common.cuh"
+#include "rank1.cuh"
 
 namespace pngf {
 namespace {
@@ -213,12 +213,13 @@ __global__ void __launch_bounds__(kThreads) dbs_fp64_kernel(SweepArgs a) {
       }
     }
     ++n_acc;
-    gather_column(a, k, pb, pe);
+    // c = W[:,k] and alpha c (block 3 of the refresh scratch, free between refreshes)
+    gather_column_ac(a, k, s_pv.alpha, rvec(a, 3, 0), pb, pe);
     tick(2);
     if (!grid_sync(ctl)) { failed = true; break; }
     tick(3);
     update_state(a, s_pv, pb, pe);
-    rank1_upper(a.W, n, a.ldw, a.cbuf, s_pv.alpha, eb, ee);
+    rank1_upper_ac(a.W, n, a.ldw, rvec(a, 3, 0), a.cbuf, eb, ee);
     __syncthreads();
     tick(4);
     ++since_refresh;
